@@ -1,0 +1,175 @@
+/*
+ * lee_lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for the Linearized Euler
+ * Equations without background velocity (Otte & Frank, "Derivation and Analysis of Lattice
+ * Boltzmann Schemes for the Linearized Euler Equations", arXiv:1601.08103).
+ *
+ * The library advances the BGK lattice Boltzmann equation of Sec. 6 (eq. "LBE update scheme"),
+ *     g_i(t+1, x + c_i) = (1 - 1/tau) g_i(t, x) + (1/tau) g_i^eq(t, x),
+ * whose equilibrium (Sec. 4 eq. "equilibrium" for monoatomic gases, Sec. 5 general form for
+ * polyatomic gases) is linear in the fluctuations (rho', u', theta').  Time, space and velocities
+ * are in lattice units (epsilon = dx = dt = 1).
+ *
+ * Conventions shared by all entry points
+ * -------------------------------------
+ *  - Cell index: cell = x + nx * (y + ny * z); unused dimensions have extent 1.
+ *  - Field layout (FP64): rho[cells], u[D][cells] (component-major), theta[cells].
+ *  - Population layout (FP64 in the API): g[q][cells] in the library's velocity order, which
+ *    lee_velset_info() reports.
+ *  - State: the device buffer holds the POST-collision populations of the current time t,
+ *    g*(t) = (1 - 1/tau) g(t) + (1/tau) g^eq(g(t)) (then damped inside a sponge frame); the next
+ *    step pulls g_i(t+1, x) = g*_i(t, x - c_i) and collides it.  Right after init_fields,
+ *    g*(0) = g(0) = g^eq(IC) (Sec. 7 initial condition), which is its own collision.
+ *  - Collision keeps rho', u' and theta' of every cell, so moments of g*(t) are those of g(t)
+ *    (except inside a sponge frame, where they include that step's damping).
+ *  - Ownership: the handle owns all device memory it allocates; caller buffers are only read or
+ *    written during the call.  `on_device` = 1 means the pointer is CUDA device memory usable on
+ *    the handle's stream, 0 means host memory (pageable or pinned).
+ *  - Asynchrony: every call is enqueued on the handle's stream.  Calls that read or write host
+ *    memory synchronise that stream before returning; device-pointer calls do not.
+ *  - Errors: every call returns a lee_status; no call throws or aborts.  After LEE_ERR_CUDA or
+ *    LEE_ERR_TIMEOUT the handle is poisoned: every later call except destroy returns
+ *    LEE_ERR_POISONED.  lee_lbm_last_error() gives a one-line reason.
+ */
+#ifndef LEE_LBM_H
+#define LEE_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LEE_OK = 0,
+    LEE_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, enum value or combination          */
+    LEE_ERR_UNSTABLE_TAU = 2,     /* tau < 1/2: |1 - 1/tau| > 1, outside the L2 stability bound */
+    LEE_ERR_OUT_OF_MEMORY = 3,    /* device allocation failed                              */
+    LEE_ERR_CUDA = 4,             /* a CUDA call failed; the handle is poisoned            */
+    LEE_ERR_NONFINITE = 5,        /* a NaN/Inf was found by lee_lbm_check_finite           */
+    LEE_ERR_TIMEOUT = 6,          /* a bounded device wait ran out; the handle is poisoned */
+    LEE_ERR_UNSUPPORTED = 7,      /* valid but not implemented combination                 */
+    LEE_ERR_POISONED = 8          /* handle unusable after an earlier CUDA error           */
+} lee_status;
+
+/* Velocity sets of Sec. 8 (values fixed by the paper; see lee_velset_info). */
+typedef enum {
+    LEE_D1Q3 = 0,          /* Sec. 8.1:   rho0 = 1,    theta0 = 1/3                      */
+    LEE_D2Q5 = 1,          /* Sec. 8.2.1: rho0 = 1,    theta0 = 1/4                      */
+    LEE_D2Q5_DIATOMIC = 2, /* Sec. 8.2.2: rho0 = 20/3, theta0 = 3/10, beta = (0, 1/2)     */
+    LEE_D3Q7 = 3,          /* Sec. 8.3.1: rho0 = 1,    theta0 = 1/5,  alpha = 0           */
+    LEE_D3Q9 = 4,          /* Sec. 8.3.1: rho0 = 1,    theta0 = 3/5,  alpha = 3/40        */
+    LEE_D3Q13 = 5,         /* Sec. 8.3.1: rho0 = 1,    theta0 = 2/5,  alpha = 0           */
+    LEE_D3Q19 = 6,         /* Sec. 8.3.1: rho0 = 1,    theta0 = 3/10, alpha = 0           */
+    LEE_D3Q7_DIATOMIC = 7  /* Sec. 8.3.2: f1 = 5/42 (rho0 = 1), theta0 = 5/21, beta = (0, 2/3) */
+} lee_velset;
+
+/* Edge treatment.  The paper treats periodic domains only (Sec. 2.2); the open variants are
+ * additions of this library:
+ *   OPEN_ZERO:    a population that would stream in from outside is the rest state, g = 0.
+ *   OPEN_SPONGE:  OPEN_ZERO, plus post-collision damping g* <- (1 - sigma(d)) g* in a frame of
+ *                 sponge_width cells, sigma(d) = sponge_strength (d / sponge_width)^2, d = depth
+ *                 of the cell in the frame (1 .. sponge_width, maximum over axes).
+ *   OPEN_LEARNED: 2D five-velocity sets only; the entering population of each edge cell is
+ *                 predicted by a small MLP from the 3-cell strip along the inward normal
+ *                 (lee_lbm_set_boundary_mlp). */
+typedef enum { LEE_BC_PERIODIC = 0, LEE_BC_OPEN_ZERO = 1, LEE_BC_OPEN_SPONGE = 2, LEE_BC_OPEN_LEARNED = 3 } lee_bc;
+
+/* Storage of the populations in device memory.  Collision arithmetic is FP64 for F64 storage and
+ * FP32 otherwise.  The 16-bit forms store S * g_i / f*_i rounded to nearest-even, with S a power
+ * of two (config.store_scale, or chosen by init_fields when 0) -- g is already the deviation from
+ * the rest state, since F = M (1 + epsilon g) (Sec. 3). */
+typedef enum { LEE_STORE_F64 = 0, LEE_STORE_F32 = 1, LEE_STORE_F16 = 2, LEE_STORE_BF16 = 3 } lee_storage;
+
+typedef struct {
+    int32_t set;            /* lee_velset                                                   */
+    int32_t storage;        /* lee_storage                                                  */
+    int64_t nx, ny, nz;     /* grid extents; ny = 1 in 1D, nz = 1 in 1D/2D                  */
+    double tau;             /* BGK relaxation time (Sec. 4); must be >= 1/2                 */
+    int32_t bc;             /* lee_bc                                                       */
+    int32_t sponge_width;   /* frame width in cells for LEE_BC_OPEN_SPONGE                  */
+    double sponge_strength; /* sigma at the outermost frame cell (0 .. 1)                   */
+    double store_scale;     /* 16-bit storage scale S (power of two), 0 = choose at init    */
+    void *cuda_stream;      /* cudaStream_t to run on; NULL = legacy default stream         */
+} lee_lbm_config;
+
+typedef struct lee_lbm lee_lbm; /* opaque solver handle */
+
+/* One-line description of a status code (static string, never NULL). */
+const char *lee_status_string(lee_status s);
+
+/* Describes velocity set `set` in the library's order.  Sec. 8 tables; general-equilibrium
+ * coefficients of Sec. 5 (monoatomic sets: a1 = 1/rho0, a2 = -D/(2 theta0), b = 1/theta0,
+ * c1 = 0, c2 = 1/theta0^2, beta = 0, gamma = (D+2)/D).
+ *   D, q:   dimension and number of velocities (q <= 27)
+ *   c:      [q][3] integer velocities (host memory, may be NULL)
+ *   f:      [q] weights f*_i (may be NULL);  beta: [q] additional energies (may be NULL)
+ *   consts: [8] = {rho0, theta0, gamma, a1, a2, b, c1, c2} (may be NULL)
+ * Returns LEE_ERR_INVALID_ARGUMENT for an unknown set or NULL D/q. */
+lee_status lee_velset_info(int32_t set, int32_t *D, int32_t *q, int32_t *c, double *f, double *beta, double *consts);
+
+/* Creates a solver for cfg on the current CUDA device.  Validates the configuration (tau >= 1/2,
+ * extents >= 1 and consistent with the dimension, storage/bc/set combination), allocates the
+ * ping-pong population buffers, field staging and reduction scratch on the device, and leaves the
+ * populations at the rest state g = 0.  *out is NULL on failure. */
+lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out);
+
+/* Sets the state to the equilibrium of the given fields, g_i = g_i^eq(rho', u', theta')
+ * (Sec. 7 initial condition; Sec. 4/5 equilibrium).  rho[cells], u[D][cells], theta[cells] in
+ * FP64.  For 16-bit storage with store_scale = 0 the scale S is chosen here: the largest power of
+ * two with S * max_i,x |g_i / f*_i| <= 1024. */
+lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, const double *theta, int32_t on_device);
+
+/* Advances n >= 0 time steps of the LBE update scheme (Sec. 6): one fused pull-stream + BGK
+ * collision kernel per step (plus the boundary network for OPEN_LEARNED).  Asynchronous. */
+lee_status lee_lbm_step(lee_lbm *h, int64_t n);
+
+/* Per-cell moments of the current state (Sec. 4 discrete moments; Sec. 5 temperature for
+ * polyatomic sets): rho'[cells], u'[D][cells], theta'[cells] in FP64.  Any pointer may be NULL
+ * to skip that output. */
+lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, int32_t on_device);
+
+/* Global FP64 sums of the current state, out[D+4]:
+ *   out[0]      sum_x rho'                             (conserved on periodic grids)
+ *   out[1..D]   sum_x sum_i c_i g_i  = rho0 sum_x u'    (conserved)
+ *   out[D+1]    sum_x sum_i (|c_i|^2 + beta_i) g_i / 2  (energy moment of Sec. 5, conserved)
+ *   out[D+2]    sum_x sum_i g_i^2 / f*_i                (weighted energy, non-increasing for
+ *                                                        tau >= 1/2; cf. A0 of Sec. 8.3.1)
+ *   out[D+3]    number of non-finite stored populations
+ * Deterministic: fixed per-block order, then one ordered pass over the block partials. */
+lee_status lee_lbm_reduce(lee_lbm *h, double *out, int32_t on_device);
+
+/* Returns LEE_ERR_NONFINITE if any stored population is NaN or Inf, else LEE_OK (host sync). */
+lee_status lee_lbm_check_finite(lee_lbm *h);
+
+/* Copies the state g*(t) out as FP64 g[q][cells] (decoded from 16-bit storage) -- checkpoint. */
+lee_status lee_lbm_get_populations(lee_lbm *h, double *g, int32_t on_device);
+
+/* Replaces the state with g[q][cells] (FP64, encoded into the storage type) -- resume.  Used
+ * with get_populations a resumed run equals the uninterrupted one bit for bit. */
+lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_device);
+
+/* Installs the boundary network for LEE_BC_OPEN_LEARNED (see lee_mlp.h for the parameter
+ * layout).  params: nparams FP32 values, host memory. */
+lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t nparams);
+
+/* Number of time steps taken since the last init/set_populations. */
+lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
+
+/* The 16-bit storage scale S in use (1 for F64/F32 storage). */
+lee_status lee_lbm_store_scale(lee_lbm *h, double *scale);
+
+/* Blocks until all work on the handle's stream has finished. */
+lee_status lee_lbm_sync(lee_lbm *h);
+
+/* Last error message of the handle (empty string if none; never NULL for a non-NULL handle). */
+const char *lee_lbm_last_error(lee_lbm *h);
+
+/* Frees the handle and its device memory.  NULL-safe.  Synchronises the stream first. */
+lee_status lee_lbm_destroy(lee_lbm *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEE_LBM_H */

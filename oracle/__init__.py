@@ -58,6 +58,8 @@ def _load():
         lib.or_step.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_double, dp, i64, dp]
         lib.or_reduce.argtypes = [ctypes.c_int, i64, dp, dp]
+        lib.or_post_state.argtypes = [ctypes.c_int, i64, i64, i64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, dp, dp]
         lib.or_set_threads.argtypes = [ctypes.c_int]
         lib.or_get_threads.restype = ctypes.c_int
         _lib = lib
@@ -155,6 +157,19 @@ def step(name: str, shape, tau: float, g, nsteps: int, bc: str = "periodic", spo
     if rc != 0:
         raise ValueError(f"or_step rejected its arguments ({rc})")
     return g
+
+
+def post_state(name: str, shape, tau: float, g, bc: str = "periodic", sponge_w: int = 0,
+               sponge_smax: float = 0.0) -> np.ndarray:
+    """Post-collision populations of g (damped inside a sponge frame): what one step streams."""
+    nx, ny, nz = (list(shape) + [1, 1])[:3]
+    g = _f64(g)
+    out = np.empty_like(g)
+    rc = _load().or_post_state(SETS[name], nx, ny, nz, float(tau), BC[bc], int(sponge_w), float(sponge_smax), _p(g),
+                               _p(out))
+    if rc != 0:
+        raise ValueError(f"or_post_state rejected its arguments ({rc})")
+    return out
 
 
 def reduce(name: str, g) -> np.ndarray:

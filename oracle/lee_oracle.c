@@ -366,6 +366,27 @@ int or_step(int id, int64_t nx, int64_t ny, int64_t nz, double tau, int bc, int 
     return 0;
 }
 
+/* Post-collision state of a field: (1 - 1/tau) g + (1/tau) g^eq(g) per cell, multiplied inside a
+ * sponge frame (bc = OR_BC_OPEN_SPONGE) by the same 1 - sigma(d) that or_step applies before
+ * streaming.  This is the state that one push step streams, i.e. the populations "in flight". */
+int or_post_state(int id, int64_t nx, int64_t ny, int64_t nz, double tau, int bc, int sponge_w, double sponge_smax,
+                  const double *g, double *out) {
+    or_set s;
+    if (build_set(id, &s) != 0) return -1;
+    const int64_t cells = nx * ny * nz;
+    const int64_t n[3] = {nx, ny, nz};
+    int rc = or_collide(id, cells, tau, g, out);
+    if (rc != 0) return rc;
+    if (bc == OR_BC_OPEN_SPONGE) {
+        for (int64_t cell = 0; cell < cells; ++cell) {
+            int64_t x = cell % nx, y = (cell / nx) % ny, z = cell / (nx * ny);
+            double damp = 1.0 - sponge_sigma(x, y, z, n, s.D, sponge_w, sponge_smax);
+            for (int i = 0; i < s.q; ++i) out[i * cells + cell] *= damp;
+        }
+    }
+    return 0;
+}
+
 /* Global sums of a population field, in FP64 with Kahan compensation:
  *   out[0]       = sum_x rho'                       (zeroth moment, conserved on periodic grids)
  *   out[1..D]    = sum_x <c_a g>_S = rho0 sum_x u'_a (momentum, conserved)

@@ -1,0 +1,317 @@
+"""Python binding of the GB300 lattice Boltzmann solver for the Linearized Euler Equations.
+
+Thin ctypes layer over ``lib/liblee_lbm.so`` (C ABI in ``include/lee_lbm.h``): it marshals
+arguments and raises :class:`LeeError` on a non-OK status.  Every step of the computation runs in
+the CUDA kernels of the library; nothing here computes on the CPU.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); FP64 and C-contiguous as the header states.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+# enums of include/lee_lbm.h
+SETS = {"D1Q3": 0, "D2Q5": 1, "D2Q5_DI": 2, "D3Q7": 3, "D3Q9": 4, "D3Q13": 5, "D3Q19": 6, "D3Q7_DI": 7}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+BC = {"periodic": 0, "open_zero": 1, "open_sponge": 2, "open_learned": 3}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+LEE_OK = 0
+LEE_ERR_INVALID_ARGUMENT = 1
+LEE_ERR_UNSTABLE_TAU = 2
+LEE_ERR_OUT_OF_MEMORY = 3
+LEE_ERR_CUDA = 4
+LEE_ERR_NONFINITE = 5
+LEE_ERR_TIMEOUT = 6
+LEE_ERR_UNSUPPORTED = 7
+LEE_ERR_POISONED = 8
+
+
+class LeeError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: status {status}"
+        if _lib is not None:
+            msg += f" ({_lib.lee_status_string(status).decode()})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class lee_lbm_config(ctypes.Structure):
+    _fields_ = [("set", ctypes.c_int32), ("storage", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("tau", ctypes.c_double), ("bc", ctypes.c_int32),
+                ("sponge_width", ctypes.c_int32), ("sponge_strength", ctypes.c_double),
+                ("store_scale", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_I32, _I64, _D, _P = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+_SIGS = {
+    "lee_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lee_velset_info": (ctypes.c_int, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P, _P, _P, _P]),
+    "lee_lbm_create": (ctypes.c_int, [ctypes.POINTER(lee_lbm_config), ctypes.POINTER(_P)]),
+    "lee_lbm_init_fields": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "lee_lbm_step": (ctypes.c_int, [_P, _I64]),
+    "lee_lbm_moments": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
+    "lee_lbm_reduce": (ctypes.c_int, [_P, _P, _I32]),
+    "lee_lbm_check_finite": (ctypes.c_int, [_P]),
+    "lee_lbm_get_populations": (ctypes.c_int, [_P, _P, _I32]),
+    "lee_lbm_set_populations": (ctypes.c_int, [_P, _P, _I32]),
+    "lee_lbm_set_boundary_mlp": (ctypes.c_int, [_P, _P, _I64]),
+    "lee_lbm_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "lee_lbm_store_scale": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
+    "lee_lbm_sync": (ctypes.c_int, [_P]),
+    "lee_lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lee_lbm_destroy": (ctypes.c_int, [_P]),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library (building it with nvcc first if it is not there).  Raises if it
+    cannot be built or loaded: there is no CPU fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            p = _build.build()
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str, handle=None):
+    if status != LEE_OK:
+        detail = ""
+        if handle:
+            detail = _lib.lee_lbm_last_error(handle).decode()
+        raise LeeError(status, where, detail)
+
+
+def _addr(x):
+    """(address, on_device) of a numpy array or torch tensor (None -> (None, 0))."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), int(x.is_cuda)
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _same_place(*bufs):
+    places = {_addr(b)[1] for b in bufs if b is not None}
+    if len(places) > 1:
+        raise ValueError("all buffers of one call must be on the host or all on the device")
+    return places.pop() if places else 0
+
+
+# ------------------------------------------------------------------------------------------
+# C entry points, same names
+# ------------------------------------------------------------------------------------------
+
+def lee_status_string(status: int) -> str:
+    return load().lee_status_string(status).decode()
+
+
+def lee_velset_info(set_name: str) -> dict:
+    """Velocity set in the library's order: D, q, c[q][3], f[q], beta[q] and the Sec. 5
+    coefficients (rho0, theta0, gamma, a1, a2, b, c1, c2)."""
+    lib = load()
+    D, q = _I32(), _I32()
+    c = (_I32 * 81)()
+    f = (_D * 27)()
+    beta = (_D * 27)()
+    consts = (_D * 8)()
+    _check(lib.lee_velset_info(SETS[set_name], ctypes.byref(D), ctypes.byref(q), ctypes.cast(c, _P),
+                               ctypes.cast(f, _P), ctypes.cast(beta, _P), ctypes.cast(consts, _P)), "lee_velset_info")
+    n = q.value
+    keys = ["rho0", "theta0", "gamma", "a1", "a2", "b", "c1", "c2"]
+    out = {"D": D.value, "q": n, "c": [tuple(c[3 * i + a] for a in range(3)) for i in range(n)],
+           "f": [f[i] for i in range(n)], "beta": [beta[i] for i in range(n)]}
+    out.update({k: consts[j] for j, k in enumerate(keys)})
+    return out
+
+
+def make_config(set_name: str, shape, tau: float, storage: str = "f64", bc: str = "periodic", sponge_width: int = 0,
+                sponge_strength: float = 0.0, store_scale: float = 0.0, stream=None) -> lee_lbm_config:
+    nx, ny, nz = (list(shape) + [1, 1])[:3]
+    cfg = lee_lbm_config()
+    cfg.set = SETS[set_name]
+    cfg.storage = STORAGE[storage]
+    cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+    cfg.tau = float(tau)
+    cfg.bc = BC[bc]
+    cfg.sponge_width = int(sponge_width)
+    cfg.sponge_strength = float(sponge_strength)
+    cfg.store_scale = float(store_scale)
+    if stream is not None:
+        cfg.cuda_stream = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    return cfg
+
+
+def lee_lbm_create(cfg: lee_lbm_config) -> int:
+    lib = load()
+    h = _P()
+    _check(lib.lee_lbm_create(ctypes.byref(cfg), ctypes.byref(h)), "lee_lbm_create")
+    return h.value
+
+
+def lee_lbm_init_fields(h, rho, u, theta):
+    on = _same_place(rho, u, theta)
+    _check(_lib.lee_lbm_init_fields(h, _addr(rho)[0], _addr(u)[0], _addr(theta)[0], on), "lee_lbm_init_fields", h)
+
+
+def lee_lbm_step(h, n: int):
+    _check(_lib.lee_lbm_step(h, int(n)), "lee_lbm_step", h)
+
+
+def lee_lbm_moments(h, rho=None, u=None, theta=None):
+    on = _same_place(rho, u, theta)
+    _check(_lib.lee_lbm_moments(h, _addr(rho)[0], _addr(u)[0], _addr(theta)[0], on), "lee_lbm_moments", h)
+
+
+def lee_lbm_reduce(h, out):
+    a, on = _addr(out)
+    _check(_lib.lee_lbm_reduce(h, a, on), "lee_lbm_reduce", h)
+
+
+def lee_lbm_check_finite(h) -> bool:
+    s = _lib.lee_lbm_check_finite(h)
+    if s == LEE_ERR_NONFINITE:
+        return False
+    _check(s, "lee_lbm_check_finite", h)
+    return True
+
+
+def lee_lbm_get_populations(h, g):
+    a, on = _addr(g)
+    _check(_lib.lee_lbm_get_populations(h, a, on), "lee_lbm_get_populations", h)
+
+
+def lee_lbm_set_populations(h, g):
+    a, on = _addr(g)
+    _check(_lib.lee_lbm_set_populations(h, a, on), "lee_lbm_set_populations", h)
+
+
+def lee_lbm_set_boundary_mlp(h, params):
+    a, on = _addr(params)
+    if on:
+        raise ValueError("boundary network parameters are read from host memory")
+    n = params.size if hasattr(params, "size") and not callable(params.size) else params.numel()
+    _check(_lib.lee_lbm_set_boundary_mlp(h, a, int(n)), "lee_lbm_set_boundary_mlp", h)
+
+
+def lee_lbm_steps_done(h) -> int:
+    v = _I64()
+    _check(_lib.lee_lbm_steps_done(h, ctypes.byref(v)), "lee_lbm_steps_done")
+    return v.value
+
+
+def lee_lbm_store_scale(h) -> float:
+    v = _D()
+    _check(_lib.lee_lbm_store_scale(h, ctypes.byref(v)), "lee_lbm_store_scale")
+    return v.value
+
+
+def lee_lbm_sync(h):
+    _check(_lib.lee_lbm_sync(h), "lee_lbm_sync", h)
+
+
+def lee_lbm_last_error(h) -> str:
+    return load().lee_lbm_last_error(h).decode()
+
+
+def lee_lbm_destroy(h):
+    if h:
+        _check(_lib.lee_lbm_destroy(h), "lee_lbm_destroy")
+
+
+class Solver:
+    """Owns one handle; methods map one-to-one onto the C entry points."""
+
+    def __init__(self, set_name: str, shape, tau: float, storage: str = "f64", bc: str = "periodic", **kw):
+        load()
+        self.set_name = set_name
+        self.info = lee_velset_info(set_name)
+        self.D, self.q = self.info["D"], self.info["q"]
+        self.shape = tuple((list(shape) + [1, 1])[:3])
+        self.cells = int(self.shape[0] * self.shape[1] * self.shape[2])
+        self.storage = storage
+        self.cfg = make_config(set_name, shape, tau, storage, bc, **kw)
+        self.h = lee_lbm_create(self.cfg)
+
+    def init_fields(self, rho, u, theta):
+        lee_lbm_init_fields(self.h, rho, u, theta)
+
+    def step(self, n: int = 1):
+        lee_lbm_step(self.h, n)
+
+    def moments(self, rho=None, u=None, theta=None):
+        lee_lbm_moments(self.h, rho, u, theta)
+
+    def reduce(self, out):
+        lee_lbm_reduce(self.h, out)
+
+    def check_finite(self) -> bool:
+        return lee_lbm_check_finite(self.h)
+
+    def get_populations(self, g):
+        lee_lbm_get_populations(self.h, g)
+
+    def set_populations(self, g):
+        lee_lbm_set_populations(self.h, g)
+
+    def set_boundary_mlp(self, params):
+        lee_lbm_set_boundary_mlp(self.h, params)
+
+    @property
+    def steps_done(self) -> int:
+        return lee_lbm_steps_done(self.h)
+
+    @property
+    def store_scale(self) -> float:
+        return lee_lbm_store_scale(self.h)
+
+    def sync(self):
+        lee_lbm_sync(self.h)
+
+    def close(self):
+        if self.h:
+            lee_lbm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

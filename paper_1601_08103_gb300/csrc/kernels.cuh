@@ -1,0 +1,511 @@
+// kernels.cuh -- device code of the lattice Boltzmann solver (sm_103a).
+//
+// Hot path: one fused pull-stream + BGK-collide kernel per time step (Sec. 6, eq. "LBE update
+// scheme").  Populations live in structure-of-arrays layout, one array per velocity, x fastest,
+// in a ping-pong pair of buffers.  With SoA and a pull step every stored population is read
+// exactly once and written exactly once per step, so DRAM traffic equals the algorithmic
+// 2 * q * sizeof(storage) bytes per cell without any shared-memory staging:
+//   - each thread owns V consecutive cells of one x-row (one 16-byte vector per velocity);
+//   - a velocity with c_x = 0 is a plain aligned vector load from row (y - c_y, z - c_z);
+//   - c_x = +1 / -1 shifts the vector by one element: the missing element comes from the
+//     neighbouring lane by warp shuffle, or by a scalar load at a row start or warp edge.
+// The collision works on per-shell sums (all weights, additional energies and coefficients of
+// the velocity sets depend on |c_i|^2 only), with the whole moment -> equilibrium -> relaxation
+// chain folded on the host into two small matrices (see CollideCoef).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "velsets.cuh"
+
+namespace lee {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------------------------
+// compile-time loops
+// ---------------------------------------------------------------------------------------------
+template <class F, int... Is>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <class S>
+__host__ __device__ constexpr bool shell_present(int s) {
+    for (int i = 0; i < S::Q; ++i)
+        if (S::shell(i) == s) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------------------------
+// storage types
+// ---------------------------------------------------------------------------------------------
+template <class T>
+struct Store;
+template <>
+struct Store<double> {
+    using C = double;  // collision arithmetic type
+    static constexpr bool scaled = false;
+    __device__ static double load(double v) { return v; }
+    __device__ static double make(double v) { return v; }
+};
+template <>
+struct Store<float> {
+    using C = float;
+    static constexpr bool scaled = false;
+    __device__ static float load(float v) { return v; }
+    __device__ static float make(float v) { return v; }
+};
+template <>
+struct Store<__half> {
+    using C = float;
+    static constexpr bool scaled = true;  // stores S * g / f*
+    __device__ static float load(__half v) { return __half2float(v); }
+    __device__ static __half make(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool scaled = true;
+    __device__ static float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 make(float v) { return __float2bfloat16_rn(v); }
+};
+
+template <int BYTES>
+struct Raw;
+template <>
+struct Raw<16> { using type = uint4; };
+template <>
+struct Raw<8> { using type = uint2; };
+template <>
+struct Raw<4> { using type = unsigned int; };
+template <>
+struct Raw<2> { using type = unsigned short; };
+
+// V consecutive elements starting at p (p aligned to V * sizeof(T)), read-only path.
+template <class T, int V>
+__device__ __forceinline__ void load_vec(const T *__restrict__ p, typename Store<T>::C (&out)[V]) {
+    if constexpr (V * sizeof(T) == 8 && sizeof(T) == 8) {
+        out[0] = Store<T>::load(__ldg(p));
+    } else {
+        using R = typename Raw<V * sizeof(T)>::type;
+        union {
+            R r;
+            T e[V];
+        } u;
+        u.r = __ldg(reinterpret_cast<const R *>(p));
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = Store<T>::load(u.e[k]);
+    }
+}
+
+template <class T, int V>
+__device__ __forceinline__ void store_vec(T *__restrict__ p, const typename Store<T>::C (&in)[V]) {
+    if constexpr (V * sizeof(T) == 8 && sizeof(T) == 8) {
+        *p = Store<T>::make(in[0]);
+    } else {
+        using R = typename Raw<V * sizeof(T)>::type;
+        union {
+            R r;
+            T e[V];
+        } u;
+#pragma unroll
+        for (int k = 0; k < V; ++k) u.e[k] = Store<T>::make(in[k]);
+        *reinterpret_cast<R *>(p) = u.r;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernel parameters
+// ---------------------------------------------------------------------------------------------
+struct GridDesc {
+    int nx, ny, nz;
+    int nxc;            // chunks per row = nx / V
+    long long nchunks;  // nxc * ny * nz
+    long long pitch;    // elements between consecutive velocity arrays
+};
+
+// Collision folded into shell space.  With P_s = sum_{i in shell s} g_i and
+// J_s = sum_{i in shell s} c_i g_i, the post-collision population of velocity i in shell t is
+//     g*_i = (1 - w) g_i + sum_s M[t][s] P_s + c_i . (sum_s N[t][s] J_s),     w = 1/tau,
+// where M and N contain w, f*, the coefficients a1, a2, b, c1, c2, gamma, theta0, rho0 and the
+// energies (|c|^2 + beta)/2 (built by the host; exact algebra of Secs. 4-6).
+template <class C>
+struct CollideCoef {
+    C one_minus_omega;
+    C M[4][4];
+    C N[4][4];
+};
+
+// Open-edge treatment for non-periodic grids.
+template <class C>
+struct OpenEdge {
+    int sponge_w;        // 0 = no sponge
+    C sponge_smax;
+    const C *ghost;      // nullptr = zero-incoming; else [4][L] entering populations (2D)
+    int ghost_L;
+};
+
+// ---------------------------------------------------------------------------------------------
+// collision of one cell (index K of the per-thread vector)
+// ---------------------------------------------------------------------------------------------
+template <class S, int K, class C, int V>
+__device__ __forceinline__ void collide_cell(const C (&g)[S::Q][V], C (&out)[S::Q][V], const CollideCoef<C> &cf) {
+    // Accumulators start at -0.0 so that the first addition folds away exactly.
+    C P[4] = {C(-0.0), C(-0.0), C(-0.0), C(-0.0)};
+    C J[4][3];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) J[s][0] = J[s][1] = J[s][2] = C(-0.0);
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int s = S::shell(i);
+        const C v = g[i][K];
+        P[s] += v;
+        static_for<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (S::c(i, a) == 1) J[s][a] += v;
+            if constexpr (S::c(i, a) == -1) J[s][a] -= v;
+        });
+    });
+    C B[4], KJ[4][3];
+    static_for<4>([&](auto T) {
+        constexpr int t = decltype(T)::value;
+        if constexpr (shell_present<S>(t)) {
+            C acc = C(-0.0);
+            static_for<4>([&](auto Sx) {
+                constexpr int s = decltype(Sx)::value;
+                if constexpr (shell_present<S>(s)) acc = fma(cf.M[t][s], P[s], acc);
+            });
+            B[t] = acc;
+            if constexpr (t > 0) {
+                static_for<S::D>([&](auto A) {
+                    constexpr int a = decltype(A)::value;
+                    C kj = C(-0.0);
+                    static_for<4>([&](auto Sx) {
+                        constexpr int s = decltype(Sx)::value;
+                        if constexpr (s > 0 && shell_present<S>(s)) kj = fma(cf.N[t][s], J[s][a], kj);
+                    });
+                    KJ[t][a] = kj;
+                });
+            }
+        }
+    });
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int t = S::shell(i);
+        C eq = B[t];
+        static_for<S::D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (S::c(i, a) == 1) eq += KJ[t][a];
+            if constexpr (S::c(i, a) == -1) eq -= KJ[t][a];
+        });
+        out[i][K] = fma(cf.one_minus_omega, g[i][K], eq);
+    });
+}
+
+template <class C>
+__device__ __forceinline__ C sponge_factor(int x, int y, int z, const GridDesc &gd, int D, int w, C smax) {
+    int d = 0;
+    const int p[3] = {x, y, z};
+    const int n[3] = {gd.nx, gd.ny, gd.nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            d = max(d, w - p[a]);
+            d = max(d, p[a] - (n[a] - 1 - w));
+        }
+    }
+    if (d <= 0) return C(1);
+    const C r = C(d) / C(w);
+    return C(1) - smax * r * r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// fused pull-stream + collide, one time step
+// ---------------------------------------------------------------------------------------------
+template <class S, class T, int V, bool OPEN>
+__global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
+                                                        CollideCoef<typename Store<T>::C> cf,
+                                                        OpenEdge<typename Store<T>::C> ob) {
+    using C = typename Store<T>::C;
+    const long long raw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = raw < gd.nchunks;
+    const long long chunk = active ? raw : gd.nchunks - 1;
+    const int lane = threadIdx.x & 31;
+    const int xc = (int)(chunk % gd.nxc);
+    const long long row = chunk / gd.nxc;
+    const int y = (int)(row % gd.ny);
+    const int z = (int)(row / gd.ny);
+    const int x0 = xc * V;
+    const bool has_left = (lane > 0) && (xc > 0);
+    const bool has_right = (lane < 31) && (xc < gd.nxc - 1);
+
+    C pull[S::Q][V];
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = S::c(i, 0), cy = S::c(i, 1), cz = S::c(i, 2);
+        int ys = y - cy, zs = z - cz;
+        bool row_out = false;
+        if constexpr (cy != 0) {
+            if (ys < 0) { if constexpr (OPEN) row_out = true; else ys += gd.ny; }
+            if (ys >= gd.ny) { if constexpr (OPEN) row_out = true; else ys -= gd.ny; }
+        }
+        if constexpr (cz != 0) {
+            if (zs < 0) { if constexpr (OPEN) row_out = true; else zs += gd.nz; }
+            if (zs >= gd.nz) { if constexpr (OPEN) row_out = true; else zs -= gd.nz; }
+        }
+        const T *rowp = src + (long long)i * gd.pitch + ((long long)zs * gd.ny + ys) * gd.nx;
+        C v[V];
+        if (!row_out) {
+            load_vec<T, V>(rowp + x0, v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) v[k] = C(0);
+            if constexpr (OPEN && S::D == 2 && cx == 0) {
+                if (ob.ghost != nullptr) {  // entering through the bottom (c_y = +1) or top edge
+                    const C *gp = ob.ghost + (cy == 1 ? 2 : 3) * ob.ghost_L + x0;
+#pragma unroll
+                    for (int k = 0; k < V; ++k) v[k] = gp[k];
+                }
+            }
+        }
+        if constexpr (cx == 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) pull[i][k] = v[k];
+        } else if constexpr (cx == 1) {
+            const C prev = __shfl_up_sync(kFull, v[V - 1], 1);
+            C left;
+            if (has_left) {
+                left = prev;
+            } else {
+                int xs = x0 - 1;
+                bool out = row_out;
+                if (xs < 0) { if constexpr (OPEN) out = true; else xs += gd.nx; }
+                left = out ? C(0) : Store<T>::load(rowp[xs]);
+                if constexpr (OPEN && S::D == 2 && cy == 0) {
+                    if (xs < 0 && ob.ghost != nullptr) left = ob.ghost[0 * ob.ghost_L + y];
+                }
+            }
+            pull[i][0] = left;
+#pragma unroll
+            for (int k = 1; k < V; ++k) pull[i][k] = v[k - 1];
+        } else {
+            const C next = __shfl_down_sync(kFull, v[0], 1);
+            C right;
+            if (has_right) {
+                right = next;
+            } else {
+                int xs = x0 + V;
+                bool out = row_out;
+                if (xs >= gd.nx) { if constexpr (OPEN) out = true; else xs -= gd.nx; }
+                right = out ? C(0) : Store<T>::load(rowp[xs]);
+                if constexpr (OPEN && S::D == 2 && cy == 0) {
+                    if (x0 + V >= gd.nx && ob.ghost != nullptr) right = ob.ghost[1 * ob.ghost_L + y];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < V - 1; ++k) pull[i][k] = v[k + 1];
+            pull[i][V - 1] = right;
+        }
+    });
+
+    C post[S::Q][V];
+    static_for<V>([&](auto Kx) { collide_cell<S, decltype(Kx)::value>(pull, post, cf); });
+
+    if constexpr (OPEN) {
+        if (ob.sponge_w > 0) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const C damp = sponge_factor<C>(x0 + k, y, z, gd, S::D, ob.sponge_w, ob.sponge_smax);
+#pragma unroll
+                for (int i = 0; i < S::Q; ++i) post[i][k] *= damp;
+            }
+        }
+    }
+
+    if (active) {
+        T *outp = dst + ((long long)z * gd.ny + y) * gd.nx + x0;
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            store_vec<T, V>(outp + (long long)i * gd.pitch, post[i]);
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// auxiliary kernels: equilibrium initialisation, moments, reductions, FP64 import/export
+// ---------------------------------------------------------------------------------------------
+
+// Per-set FP64 constants for the auxiliary kernels (general form of Sec. 5).
+struct SetConsts {
+    double rho0, theta0, gamma, a1, a2, b, c1, c2;
+    double f[4];     // f* per shell
+    double beta[4];  // beta per shell
+    double scale;    // 16-bit storage scale S (1 otherwise)
+};
+
+template <class S>
+__device__ __forceinline__ double decode(double stored, int i, const SetConsts &k, bool scaled) {
+    return scaled ? stored * (k.f[S::shell(i)] / k.scale) : stored;
+}
+
+// g_i = g_i^eq(rho', u', theta') (Sec. 7 initial condition), encoded into storage type T.
+template <class S, class T>
+__global__ void k_init_equilibrium(const double *__restrict__ rho, const double *__restrict__ u,
+                                   const double *__restrict__ theta, T *__restrict__ g, long long cells, long long pitch,
+                                   SetConsts k) {
+    constexpr bool scaled = Store<T>::scaled;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[x], th = theta[x];
+        double uu[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < S::D; ++a) uu[a] = u[(long long)a * cells + x];
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = S::shell(i);
+            double cu = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cu += S::c(i, a) * uu[a];
+            const double bracket = k.a1 * r + k.a2 * th + k.b * cu + 0.5 * (double)s * (k.c1 * r + k.c2 * th);
+            const double v = scaled ? bracket * k.scale : bracket * k.f[s];
+            g[(long long)i * pitch + x] = Store<T>::make((typename Store<T>::C)v);
+        });
+    }
+}
+
+// Largest |g_i^eq / f*_i| of the initial fields, as float bits for atomicMax (non-negative floats
+// order like their bit patterns).
+template <class S>
+__global__ void k_init_maxabs(const double *__restrict__ rho, const double *__restrict__ u,
+                              const double *__restrict__ theta, long long cells, SetConsts k,
+                              unsigned int *__restrict__ maxbits) {
+    float m = 0.f;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        const double r = rho[x], th = theta[x];
+        double uu[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < S::D; ++a) uu[a] = u[(long long)a * cells + x];
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = S::shell(i);
+            double cu = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cu += S::c(i, a) * uu[a];
+            const double bracket = k.a1 * r + k.a2 * th + k.b * cu + 0.5 * (double)s * (k.c1 * r + k.c2 * th);
+            m = fmaxf(m, (float)fabs(bracket));
+        });
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(m));
+}
+
+// Per-cell moments (Sec. 4 discrete moments, Sec. 5 temperature) in FP64.
+template <class S, class T>
+__global__ void k_moments(const T *__restrict__ g, long long cells, long long pitch, SetConsts k, double *__restrict__ rho,
+                          double *__restrict__ u, double *__restrict__ theta) {
+    constexpr bool scaled = Store<T>::scaled;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        double r = 0.0, e = 0.0, j[3] = {0.0, 0.0, 0.0};
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = S::shell(i);
+            const double v = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
+            r += v;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) j[a] += S::c(i, a) * v;
+            e += 0.5 * ((double)s + k.beta[s]) * v;
+        });
+        if (rho) rho[x] = r;
+        if (u) {
+#pragma unroll
+            for (int a = 0; a < S::D; ++a) u[(long long)a * cells + x] = j[a] / k.rho0;
+        }
+        if (theta) theta[x] = ((k.gamma - 1.0) * e - k.theta0 * r) / k.rho0;
+    }
+}
+
+constexpr int kReduceThreads = 256;
+constexpr int kReduceMax = 8;  // D + 4 <= 7 values, padded
+
+// Block partial sums of the D + 4 diagnostics (see lee_lbm_reduce), fixed order per block.
+template <class S, class T>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ g, long long cells, long long pitch,
+                                                                   SetConsts k, double *__restrict__ partial) {
+    constexpr bool scaled = Store<T>::scaled;
+    constexpr int NV = S::D + 4;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = S::shell(i);
+            const double v = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
+            if (!isfinite(v)) {
+                acc[NV - 1] += 1.0;
+            } else {
+                acc[0] += v;
+#pragma unroll
+                for (int a = 0; a < S::D; ++a) acc[1 + a] += S::c(i, a) * v;
+                acc[S::D + 1] += 0.5 * ((double)s + k.beta[s]) * v;
+                acc[S::D + 2] += v * v / k.f[s];
+            }
+        });
+    }
+    __shared__ double sh[kReduceThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double a = acc[v];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
+        if (lane == 0) sh[warp][v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) a += sh[w][threadIdx.x];
+        partial[(long long)blockIdx.x * kReduceMax + threadIdx.x] = a;
+    }
+}
+
+// Ordered sum of the block partials (one warp per output value).
+__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out);
+
+// FP64 [q][cells] <-> storage (checkpoint export / import).
+template <class S, class T>
+__global__ void k_export(const T *__restrict__ g, long long cells, long long pitch, SetConsts k, double *__restrict__ out) {
+    constexpr bool scaled = Store<T>::scaled;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            out[(long long)i * cells + x] = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
+        });
+    }
+}
+
+template <class S, class T>
+__global__ void k_import(const double *__restrict__ in, long long cells, long long pitch, SetConsts k, T *__restrict__ g) {
+    constexpr bool scaled = Store<T>::scaled;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int s = S::shell(i);
+            const double v = in[(long long)i * cells + x];
+            const double st = scaled ? v * (k.scale / k.f[s]) : v;
+            g[(long long)i * pitch + x] = Store<T>::make((typename Store<T>::C)st);
+        });
+    }
+}
+
+}  // namespace lee

@@ -1,0 +1,468 @@
+// lee_lbm.cu -- C ABI of the solver (include/lee_lbm.h): handle, memory, validation, dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lee_lbm.h"
+#include "ops.cuh"
+
+namespace lee {
+extern const SetOps kOpsD1Q3, kOpsD2Q5, kOpsD2Q5Di, kOpsD3Q7, kOpsD3Q7Di, kOpsD3Q9, kOpsD3Q13, kOpsD3Q19;
+
+const SetOps *set_ops(int set) {
+    switch (set) {
+    case LEE_D1Q3: return &kOpsD1Q3;
+    case LEE_D2Q5: return &kOpsD2Q5;
+    case LEE_D2Q5_DIATOMIC: return &kOpsD2Q5Di;
+    case LEE_D3Q7: return &kOpsD3Q7;
+    case LEE_D3Q9: return &kOpsD3Q9;
+    case LEE_D3Q13: return &kOpsD3Q13;
+    case LEE_D3Q19: return &kOpsD3Q19;
+    case LEE_D3Q7_DIATOMIC: return &kOpsD3Q7Di;
+    default: return nullptr;
+    }
+}
+
+__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out) {
+    const int v = blockIdx.x;  // one block (one warp) per output value
+    if (v >= nv) return;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) a += partial[(long long)b * kReduceMax + v];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
+    if (threadIdx.x == 0) out[v] = a;
+}
+
+SetConsts consts_for(int set, double scale) {
+    SetConsts k{};
+    dispatch_set(set, [&](auto s) {
+        using S = decltype(s);
+        k = host_consts<S>(scale);
+    });
+    return k;
+}
+
+// Folded collision coefficients (see CollideCoef in kernels.cuh):
+//   rho' = sum_s w1_s P_s,  e = sum_s w2_s P_s,  theta' = kE e - kR rho',  j = sum_s w1_s J_s,
+//   g*_i = (1 - w) g_i + w f'_t (alpha_t rho' + beta_t theta') + w f'_t (b / rho0) c_i . j
+// with w1_s = f*_s for the scaled 16-bit storage (stored value S g / f*) and 1 otherwise,
+// w2_s = w1_s (s + beta_s) / 2, f'_t = 1 (scaled) or f*_t, alpha_t = a1 + t c1 / 2,
+// beta_t = a2 + t c2 / 2, kE = (gamma - 1) / rho0, kR = theta0 / rho0 (Secs. 4-6).
+void fold_coefficients(int set, bool scaled, double omega, double M[4][4], double N[4][4]) {
+    const SetConsts k = consts_for(set, 1.0);
+    for (int t = 0; t < 4; ++t)
+        for (int s = 0; s < 4; ++s) M[t][s] = N[t][s] = 0.0;
+    const double kE = (k.gamma - 1.0) / k.rho0, kR = k.theta0 / k.rho0;
+    for (int t = 0; t < 4; ++t) {
+        const double ft = scaled ? 1.0 : k.f[t];
+        const double alpha = k.a1 + 0.5 * t * k.c1, beta = k.a2 + 0.5 * t * k.c2;
+        for (int s = 0; s < 4; ++s) {
+            const double w1 = scaled ? k.f[s] : 1.0;
+            const double w2 = 0.5 * (s + k.beta[s]) * w1;
+            M[t][s] = omega * ft * (alpha * w1 + beta * (kE * w2 - kR * w1));
+            N[t][s] = omega * ft * (k.b / k.rho0) * w1;
+        }
+    }
+}
+
+}  // namespace lee
+
+using namespace lee;
+
+struct lee_lbm {
+    lee_lbm_config cfg{};
+    const SetOps *ops = nullptr;
+    int device = 0;
+    int D = 0, Q = 0;
+    long long cells = 0, pitch = 0;
+    size_t elem = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *fields = nullptr;  // (D + 2) * cells FP64 staging for host fields
+    double *pops64 = nullptr;  // Q * cells FP64 staging for host populations
+    double *partial = nullptr;
+    int nblocks = 0;
+    double *red_out = nullptr;
+    unsigned int *maxbits = nullptr;
+    cudaStream_t st = nullptr;
+    long long steps = 0;
+    double scale = 1.0;
+    bool poisoned = false;
+    std::string err;
+    // learned boundary
+    void *ghost = nullptr;
+    int ghost_L = 0;
+    float *mlp = nullptr;
+    long long mlp_n = 0;
+};
+
+namespace {
+
+lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
+    if (h) {
+        h->err = msg;
+        if (s == LEE_ERR_CUDA || s == LEE_ERR_TIMEOUT) h->poisoned = true;
+    }
+    return s;
+}
+
+lee_status cuda_fail(lee_lbm *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, LEE_ERR_OUT_OF_MEMORY, m);
+    return fail(h, LEE_ERR_CUDA, m);
+}
+
+#define LEE_CK(h, call, what)                                 \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, what); \
+    } while (0)
+
+lee_status enter(lee_lbm *h) {
+    if (!h) return LEE_ERR_INVALID_ARGUMENT;
+    if (h->poisoned) return LEE_ERR_POISONED;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    return LEE_OK;
+}
+
+size_t elem_size(int storage) {
+    switch (storage) {
+    case LEE_STORE_F64: return 8;
+    case LEE_STORE_F32: return 4;
+    case LEE_STORE_F16:
+    case LEE_STORE_BF16: return 2;
+    default: return 0;
+    }
+}
+
+void free_all(lee_lbm *h) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->fields);
+    cudaFree(h->pops64);
+    cudaFree(h->partial);
+    cudaFree(h->red_out);
+    cudaFree(h->maxbits);
+    cudaFree(h->ghost);
+    cudaFree(h->mlp);
+}
+
+lee_status ensure_fields(lee_lbm *h) {
+    if (h->fields) return LEE_OK;
+    LEE_CK(h, cudaMalloc(&h->fields, sizeof(double) * (size_t)(h->D + 2) * (size_t)h->cells), "cudaMalloc(fields)");
+    return LEE_OK;
+}
+
+lee_status ensure_pops64(lee_lbm *h) {
+    if (h->pops64) return LEE_OK;
+    LEE_CK(h, cudaMalloc(&h->pops64, sizeof(double) * (size_t)h->Q * (size_t)h->cells), "cudaMalloc(pops64)");
+    return LEE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lee_status_string(lee_status s) {
+    switch (s) {
+    case LEE_OK: return "ok";
+    case LEE_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case LEE_ERR_UNSTABLE_TAU: return "tau < 1/2 is outside the L2 stability bound";
+    case LEE_ERR_OUT_OF_MEMORY: return "device out of memory";
+    case LEE_ERR_CUDA: return "CUDA error (handle poisoned)";
+    case LEE_ERR_NONFINITE: return "non-finite population found";
+    case LEE_ERR_TIMEOUT: return "bounded device wait timed out (handle poisoned)";
+    case LEE_ERR_UNSUPPORTED: return "unsupported combination";
+    case LEE_ERR_POISONED: return "handle poisoned by an earlier CUDA error";
+    default: return "unknown status";
+    }
+}
+
+lee_status lee_velset_info(int32_t set, int32_t *D, int32_t *q, int32_t *c, double *f, double *beta, double *consts) {
+    const SetOps *o = set_ops(set);
+    if (!o || !D || !q) return LEE_ERR_INVALID_ARGUMENT;
+    *D = o->D;
+    *q = o->Q;
+    const SetConsts k = consts_for(set, 1.0);
+    for (int i = 0; i < o->Q; ++i) {
+        if (c)
+            for (int a = 0; a < 3; ++a) c[3 * i + a] = o->c[i][a];
+        if (f) f[i] = k.f[o->shell[i]];
+        if (beta) beta[i] = k.beta[o->shell[i]];
+    }
+    if (consts) {
+        const double v[8] = {k.rho0, k.theta0, k.gamma, k.a1, k.a2, k.b, k.c1, k.c2};
+        for (int j = 0; j < 8; ++j) consts[j] = v[j];
+    }
+    return LEE_OK;
+}
+
+lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
+    if (!out) return LEE_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!cfg) return LEE_ERR_INVALID_ARGUMENT;
+    const SetOps *o = set_ops(cfg->set);
+    if (!o) return LEE_ERR_INVALID_ARGUMENT;
+    if (elem_size(cfg->storage) == 0) return LEE_ERR_INVALID_ARGUMENT;
+    if (!(cfg->tau == cfg->tau) || !std::isfinite(cfg->tau)) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->tau < 0.5) return LEE_ERR_UNSTABLE_TAU;
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return LEE_ERR_INVALID_ARGUMENT;
+    if (o->D < 3 && cfg->nz != 1) return LEE_ERR_INVALID_ARGUMENT;
+    if (o->D < 2 && cfg->ny != 1) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->nx > (1LL << 30) || cfg->ny > (1LL << 30) || cfg->nz > (1LL << 30)) return LEE_ERR_INVALID_ARGUMENT;
+    const long long cells = cfg->nx * cfg->ny * cfg->nz;
+    if (cells >= (1LL << 31)) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->bc < LEE_BC_PERIODIC || cfg->bc > LEE_BC_OPEN_LEARNED) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->bc == LEE_BC_OPEN_SPONGE) {
+        if (cfg->sponge_width < 1 || !(cfg->sponge_strength >= 0.0 && cfg->sponge_strength <= 1.0))
+            return LEE_ERR_INVALID_ARGUMENT;
+        for (int a = 0; a < o->D; ++a) {
+            const long long n = a == 0 ? cfg->nx : (a == 1 ? cfg->ny : cfg->nz);
+            if (2LL * cfg->sponge_width >= n) return LEE_ERR_INVALID_ARGUMENT;
+        }
+    }
+    if (cfg->bc == LEE_BC_OPEN_LEARNED && !(o->D == 2 && o->Q == 5)) return LEE_ERR_UNSUPPORTED;
+    if (cfg->bc == LEE_BC_OPEN_LEARNED && (cfg->nx < 3 || cfg->ny < 3)) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->store_scale < 0.0 || !std::isfinite(cfg->store_scale)) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->store_scale > 0.0) {
+        int ex = 0;
+        if (std::frexp(cfg->store_scale, &ex) != 0.5) return LEE_ERR_INVALID_ARGUMENT;  // power of two
+    }
+
+    lee_lbm *h = new (std::nothrow) lee_lbm();
+    if (!h) return LEE_ERR_OUT_OF_MEMORY;
+    h->cfg = *cfg;
+    h->ops = o;
+    h->D = o->D;
+    h->Q = o->Q;
+    h->cells = cells;
+    h->pitch = (cells + 63) / 64 * 64;
+    h->elem = elem_size(cfg->storage);
+    h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+    const bool is16 = cfg->storage == LEE_STORE_F16 || cfg->storage == LEE_STORE_BF16;
+    h->scale = is16 ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
+    cudaError_t e = cudaGetDevice(&h->device);
+    const size_t bytes = h->elem * (size_t)h->Q * (size_t)h->pitch;
+    if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
+    h->nblocks = aux_blocks(cells, kReduceThreads);
+    if (e == cudaSuccess) e = cudaMalloc(&h->partial, sizeof(double) * kReduceMax * (size_t)h->nblocks);
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_out, sizeof(double) * kReduceMax);
+    if (e == cudaSuccess) e = cudaMalloc(&h->maxbits, sizeof(unsigned int));
+    if (e == cudaSuccess && cfg->bc == LEE_BC_OPEN_LEARNED) {
+        h->ghost_L = (int)(cfg->nx > cfg->ny ? cfg->nx : cfg->ny);
+        e = cudaMalloc(&h->ghost, (cfg->storage == LEE_STORE_F64 ? 8 : 4) * 4 * (size_t)h->ghost_L);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        lee_status s = e == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA;
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return s;
+    }
+    *out = h;
+    return LEE_OK;
+}
+
+lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, const double *theta, int32_t on_device) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!rho || !theta || (h->D > 0 && !u)) return fail(h, LEE_ERR_INVALID_ARGUMENT, "init_fields: NULL field");
+    const double *dr = rho, *du = u, *dt = theta;
+    if (!on_device) {
+        if ((s = ensure_fields(h)) != LEE_OK) return s;
+        const size_t n = sizeof(double) * (size_t)h->cells;
+        double *fr = h->fields, *fu = h->fields + h->cells, *ft = h->fields + (size_t)(h->D + 1) * h->cells;
+        LEE_CK(h, cudaMemcpyAsync(fr, rho, n, cudaMemcpyHostToDevice, h->st), "H2D rho");
+        LEE_CK(h, cudaMemcpyAsync(fu, u, n * h->D, cudaMemcpyHostToDevice, h->st), "H2D u");
+        LEE_CK(h, cudaMemcpyAsync(ft, theta, n, cudaMemcpyHostToDevice, h->st), "H2D theta");
+        dr = fr;
+        du = fu;
+        dt = ft;
+    }
+    const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
+    if (is16 && h->cfg.store_scale == 0.0) {
+        LEE_CK(h, cudaMemsetAsync(h->maxbits, 0, sizeof(unsigned int), h->st), "memset maxbits");
+        LEE_CK(h, h->ops->init_maxabs(dr, du, dt, h->cells, consts_for(h->cfg.set, 1.0), h->maxbits, h->st), "init_maxabs");
+        unsigned int bits = 0;
+        LEE_CK(h, cudaMemcpyAsync(&bits, h->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, h->st), "D2H maxbits");
+        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+        float m;
+        std::memcpy(&m, &bits, sizeof(m));
+        double S = 1.0;
+        if (m > 0.0f && std::isfinite(m)) {
+            // largest power of two with S * m <= 1024
+            int ex = (int)std::floor(std::log2(1024.0 / (double)m));
+            S = std::ldexp(1.0, ex);
+        }
+        h->scale = S;
+    }
+    const SetConsts k = consts_for(h->cfg.set, h->scale);
+    LEE_CK(h, h->ops->init(h->cfg.storage, dr, du, dt, h->buf[0], h->cells, h->pitch, k, h->st), "init kernel");
+    h->cur = 0;
+    h->steps = 0;
+    if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (n < 0) return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: n < 0");
+    if (h->cfg.bc == LEE_BC_OPEN_LEARNED) return fail(h, LEE_ERR_UNSUPPORTED, "learned boundary not installed");
+    StepLaunch L{};
+    L.storage = h->cfg.storage;
+    L.nx = (int)h->cfg.nx;
+    L.ny = (int)h->cfg.ny;
+    L.nz = (int)h->cfg.nz;
+    L.pitch = h->pitch;
+    L.open = h->cfg.bc != LEE_BC_PERIODIC;
+    L.omega = 1.0 / h->cfg.tau;
+    const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
+    fold_coefficients(h->cfg.set, is16, L.omega, L.coefM, L.coefN);
+    L.sponge_w = h->cfg.bc == LEE_BC_OPEN_SPONGE ? h->cfg.sponge_width : 0;
+    L.sponge_smax = h->cfg.sponge_strength;
+    L.ghost = nullptr;
+    L.ghost_L = 0;
+    L.force_scalar = 0;
+    L.stream = h->st;
+    for (int64_t t = 0; t < n; ++t) {
+        L.src = h->buf[h->cur];
+        L.dst = h->buf[h->cur ^ 1];
+        LEE_CK(h, h->ops->step(L), "stream_collide launch");
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return LEE_OK;
+}
+
+lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, int32_t on_device) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    const SetConsts k = consts_for(h->cfg.set, h->scale);
+    if (on_device) {
+        LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, rho, u, theta, h->st), "moments");
+        return LEE_OK;
+    }
+    if ((s = ensure_fields(h)) != LEE_OK) return s;
+    double *fr = h->fields, *fu = h->fields + h->cells, *ft = h->fields + (size_t)(h->D + 1) * h->cells;
+    LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, fr, fu, ft, h->st), "moments");
+    const size_t n = sizeof(double) * (size_t)h->cells;
+    if (rho) LEE_CK(h, cudaMemcpyAsync(rho, fr, n, cudaMemcpyDeviceToHost, h->st), "D2H rho");
+    if (u) LEE_CK(h, cudaMemcpyAsync(u, fu, n * h->D, cudaMemcpyDeviceToHost, h->st), "D2H u");
+    if (theta) LEE_CK(h, cudaMemcpyAsync(theta, ft, n, cudaMemcpyDeviceToHost, h->st), "D2H theta");
+    LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_reduce(lee_lbm *h, double *out, int32_t on_device) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!out) return fail(h, LEE_ERR_INVALID_ARGUMENT, "reduce: NULL out");
+    const SetConsts k = consts_for(h->cfg.set, h->scale);
+    const int nv = h->D + 4;
+    LEE_CK(h, h->ops->reduce_partial(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, h->partial, h->nblocks, h->st),
+           "reduce_partial");
+    double *dst = on_device ? out : h->red_out;
+    k_reduce_final<<<nv, 32, 0, h->st>>>(h->partial, h->nblocks, nv, dst);
+    LEE_CK(h, cudaGetLastError(), "reduce_final");
+    if (!on_device) {
+        LEE_CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->st), "D2H reduce");
+        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    }
+    return LEE_OK;
+}
+
+lee_status lee_lbm_check_finite(lee_lbm *h) {
+    double out[kReduceMax];
+    lee_status s = lee_lbm_reduce(h, out, 0);
+    if (s != LEE_OK) return s;
+    if (out[h->D + 3] != 0.0) return fail(h, LEE_ERR_NONFINITE, "non-finite populations present");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_get_populations(lee_lbm *h, double *g, int32_t on_device) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!g) return fail(h, LEE_ERR_INVALID_ARGUMENT, "get_populations: NULL");
+    const SetConsts k = consts_for(h->cfg.set, h->scale);
+    double *dst = g;
+    if (!on_device) {
+        if ((s = ensure_pops64(h)) != LEE_OK) return s;
+        dst = h->pops64;
+    }
+    LEE_CK(h, h->ops->export_f64(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, dst, h->st), "export");
+    if (!on_device) {
+        LEE_CK(h, cudaMemcpyAsync(g, dst, sizeof(double) * (size_t)h->Q * h->cells, cudaMemcpyDeviceToHost, h->st), "D2H g");
+        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    }
+    return LEE_OK;
+}
+
+lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_device) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!g) return fail(h, LEE_ERR_INVALID_ARGUMENT, "set_populations: NULL");
+    const SetConsts k = consts_for(h->cfg.set, h->scale);
+    const double *src = g;
+    if (!on_device) {
+        if ((s = ensure_pops64(h)) != LEE_OK) return s;
+        LEE_CK(h, cudaMemcpyAsync(h->pops64, g, sizeof(double) * (size_t)h->Q * h->cells, cudaMemcpyHostToDevice, h->st),
+               "H2D g");
+        src = h->pops64;
+    }
+    h->cur = 0;
+    LEE_CK(h, h->ops->import_f64(h->cfg.storage, src, h->cells, h->pitch, k, h->buf[0], h->st), "import");
+    h->steps = 0;
+    if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t nparams) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    (void)params;
+    (void)nparams;
+    return fail(h, LEE_ERR_UNSUPPORTED, "learned boundary not built yet");
+}
+
+lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
+    if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
+    *steps = h->steps;
+    return LEE_OK;
+}
+
+lee_status lee_lbm_store_scale(lee_lbm *h, double *scale) {
+    if (!h || !scale) return LEE_ERR_INVALID_ARGUMENT;
+    *scale = h->scale;
+    return LEE_OK;
+}
+
+lee_status lee_lbm_sync(lee_lbm *h) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    return LEE_OK;
+}
+
+const char *lee_lbm_last_error(lee_lbm *h) { return h ? h->err.c_str() : "NULL handle"; }
+
+lee_status lee_lbm_destroy(lee_lbm *h) {
+    if (!h) return LEE_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+    cudaGetLastError();
+    return LEE_OK;
+}
+
+}  // extern "C"

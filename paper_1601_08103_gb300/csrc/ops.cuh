@@ -1,0 +1,86 @@
+// ops.cuh -- per-velocity-set launch table.  Each translation unit set_*.cu instantiates the
+// kernels of a few sets (so that the library compiles in parallel) and exports one SetOps per
+// set; lee_lbm.cu only sees these tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace lee {
+
+// Launch description of one fused time step.
+struct StepLaunch {
+    int storage;         // lee_storage
+    const void *src;
+    void *dst;
+    int nx, ny, nz;
+    long long pitch;
+    bool open;
+    double omega;        // 1 / tau
+    double coefM[4][4];  // see CollideCoef
+    double coefN[4][4];
+    int sponge_w;
+    double sponge_smax;
+    const void *ghost;   // float (or double for F64) [4][ghost_L], or nullptr
+    int ghost_L;
+    int force_scalar;    // 1: use the one-cell-per-thread variant (testing)
+    cudaStream_t stream;
+};
+
+struct SetOps {
+    int D, Q;
+    // one fused pull-stream + collide step
+    cudaError_t (*step)(const StepLaunch &);
+    // g = g^eq(fields) (fields FP64 on device)
+    cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
+                        long long pitch, const SetConsts &k, cudaStream_t st);
+    // max |g^eq / f*| of the fields into *maxbits (float bits; caller zeroes it)
+    cudaError_t (*init_maxabs)(const double *rho, const double *u, const double *theta, long long cells, const SetConsts &k,
+                               unsigned int *maxbits, cudaStream_t st);
+    cudaError_t (*moments)(int storage, const void *g, long long cells, long long pitch, const SetConsts &k, double *rho,
+                           double *u, double *theta, cudaStream_t st);
+    // partial sums: writes nblocks * kReduceMax doubles
+    cudaError_t (*reduce_partial)(int storage, const void *g, long long cells, long long pitch, const SetConsts &k,
+                                  double *partial, int nblocks, cudaStream_t st);
+    cudaError_t (*export_f64)(int storage, const void *g, long long cells, long long pitch, const SetConsts &k, double *out,
+                              cudaStream_t st);
+    cudaError_t (*import_f64)(int storage, const double *in, long long cells, long long pitch, const SetConsts &k, void *g,
+                              cudaStream_t st);
+    // description for lee_velset_info
+    int c[27][3];
+    int shell[27];
+};
+
+const SetOps *set_ops(int set);
+
+// Host-side velocity-set constants (the same compile-time tables the kernels use).
+template <class S>
+SetConsts host_consts(double scale) {
+    SetConsts k{};
+    k.rho0 = S::rho0;
+    k.theta0 = S::theta0;
+    k.gamma = S::gamma;
+    k.a1 = S::a1;
+    k.a2 = S::a2;
+    k.b = S::b;
+    k.c1 = S::c1;
+    k.c2 = S::c2;
+    for (int s = 0; s < 4; ++s) {
+        k.f[s] = S::fs(s);
+        k.beta[s] = S::betas(s);
+    }
+    k.scale = scale;
+    return k;
+}
+
+// Grid size for grid-stride auxiliary kernels.
+inline int aux_blocks(long long cells, int threads = 256) {
+    long long b = (cells + threads - 1) / threads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace lee

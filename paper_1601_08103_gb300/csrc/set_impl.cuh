@@ -1,0 +1,138 @@
+// set_impl.cuh -- host launchers for one velocity set, instantiated by the set_*.cu units.
+#pragma once
+
+#include "ops.cuh"
+
+namespace lee {
+
+template <class S, class T, int V, bool OPEN>
+cudaError_t launch_step_v(const StepLaunch &L) {
+    using C = typename Store<T>::C;
+    GridDesc gd;
+    gd.nx = L.nx;
+    gd.ny = L.ny;
+    gd.nz = L.nz;
+    gd.nxc = L.nx / V;
+    gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
+    gd.pitch = L.pitch;
+    CollideCoef<C> cf;
+    cf.one_minus_omega = (C)(1.0 - L.omega);
+    for (int t = 0; t < 4; ++t)
+        for (int s = 0; s < 4; ++s) {
+            cf.M[t][s] = (C)L.coefM[t][s];
+            cf.N[t][s] = (C)L.coefN[t][s];
+        }
+    OpenEdge<C> ob;
+    ob.sponge_w = L.sponge_w;
+    ob.sponge_smax = (C)L.sponge_smax;
+    ob.ghost = static_cast<const C *>(L.ghost);
+    ob.ghost_L = L.ghost_L;
+    const long long blocks = (gd.nchunks + 255) / 256;
+    k_stream_collide<S, T, V, OPEN><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
+                                                                              static_cast<T *>(L.dst), gd, cf, ob);
+    return cudaGetLastError();
+}
+
+// Vector width: one 16-byte access per velocity and thread (8 bytes for the 19-velocity set, to
+// bound register use); one cell per thread when nx is not a multiple of the width.
+template <class S, class T>
+constexpr int vec_width() {
+    constexpr int bytes = (S::Q > 13) ? 8 : 16;
+    constexpr int v = bytes / (int)sizeof(T);
+    return v < 1 ? 1 : v;
+}
+
+template <class S, class T>
+cudaError_t launch_step_t(const StepLaunch &L) {
+    constexpr int V = vec_width<S, T>();
+    if constexpr (V > 1) {
+        if (!L.force_scalar && L.nx % V == 0)
+            return L.open ? launch_step_v<S, T, V, true>(L) : launch_step_v<S, T, V, false>(L);
+    }
+    return L.open ? launch_step_v<S, T, 1, true>(L) : launch_step_v<S, T, 1, false>(L);
+}
+
+template <class Fn>
+cudaError_t with_storage(int storage, Fn &&fn) {
+    switch (storage) {
+    case LEE_STORE_F64: return fn((double *)nullptr);
+    case LEE_STORE_F32: return fn((float *)nullptr);
+    case LEE_STORE_F16: return fn((__half *)nullptr);
+    case LEE_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class S>
+struct SetImpl {
+    static cudaError_t step(const StepLaunch &L) {
+        return with_storage(L.storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            return launch_step_t<S, T>(L);
+        });
+    }
+    static cudaError_t init(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
+                            long long pitch, const SetConsts &k, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_init_equilibrium<S, T><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, static_cast<T *>(g), cells, pitch, k);
+            return cudaGetLastError();
+        });
+    }
+    static cudaError_t init_maxabs(const double *rho, const double *u, const double *theta, long long cells,
+                                   const SetConsts &k, unsigned int *maxbits, cudaStream_t st) {
+        k_init_maxabs<S><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, cells, k, maxbits);
+        return cudaGetLastError();
+    }
+    static cudaError_t moments(int storage, const void *g, long long cells, long long pitch, const SetConsts &k, double *rho,
+                               double *u, double *theta, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_moments<S, T><<<aux_blocks(cells), 256, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, rho, u, theta);
+            return cudaGetLastError();
+        });
+    }
+    static cudaError_t reduce_partial(int storage, const void *g, long long cells, long long pitch, const SetConsts &k,
+                                      double *partial, int nblocks, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_reduce_partial<S, T><<<nblocks, kReduceThreads, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, partial);
+            return cudaGetLastError();
+        });
+    }
+    static cudaError_t export_f64(int storage, const void *g, long long cells, long long pitch, const SetConsts &k,
+                                  double *out, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_export<S, T><<<aux_blocks(cells), 256, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, out);
+            return cudaGetLastError();
+        });
+    }
+    static cudaError_t import_f64(int storage, const double *in, long long cells, long long pitch, const SetConsts &k,
+                                  void *g, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_import<S, T><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, k, static_cast<T *>(g));
+            return cudaGetLastError();
+        });
+    }
+    static SetOps make() {
+        SetOps o{};
+        o.D = S::D;
+        o.Q = S::Q;
+        o.step = &step;
+        o.init = &init;
+        o.init_maxabs = &init_maxabs;
+        o.moments = &moments;
+        o.reduce_partial = &reduce_partial;
+        o.export_f64 = &export_f64;
+        o.import_f64 = &import_f64;
+        for (int i = 0; i < S::Q; ++i) {
+            for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
+            o.shell[i] = S::shell(i);
+        }
+        return o;
+    }
+};
+
+}  // namespace lee

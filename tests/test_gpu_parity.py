@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+The library holds the post-collision state g*(t) = H(tau) g(t) (see include/lee_lbm.h); the
+oracle holds the paper's pre-collision g(t).  So populations are compared with
+oracle.collide(g(t)) (damped in a sponge frame), and moments directly (collision keeps them).
+
+Tolerances (relative L2 over all compared values, plus an element-wise max check):
+  FP64 storage: 1e-12 (the required FP64 bound);
+  FP32 storage: 1e-5  (unit roundoff 6e-8, ~10 roundings per value and step, random walk over
+                       at most 200 steps: 6e-8 * sqrt(2000) = 2.7e-6, with margin);
+  16-bit:       measured storage error, bounded loosely by u * sqrt(10 n) * 4 (u = 2^-11 FP16,
+                2^-8 BF16).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analysis as an
+from paper_1601_08103_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SETS = ["D1Q3", "D2Q5", "D2Q5_DI", "D3Q7", "D3Q9", "D3Q13", "D3Q19", "D3Q7_DI"]
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def perm_to_lib(lee, name):
+    """Index array p with oracle_array[p] in the library's velocity order."""
+    lib_c = lee.lee_velset_info(name)["c"]
+    ora = oracle.velset(name)
+    idx = {tuple(int(v) for v in c): j for j, c in enumerate(ora.c)}
+    return np.array([idx[tuple(c)] for c in lib_c])
+
+
+def shapes_for(D, vector=True):
+    if D == 1:
+        return [(1024, 1, 1)] if vector else [(1027, 1, 1)]
+    if D == 2:
+        return [(260, 37, 1)] if vector else [(129, 33, 1)]
+    return [(36, 10, 7)] if vector else [(13, 11, 3)]
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def assert_close(got, want, tol, what):
+    r = rel_l2(got, want)
+    m = np.abs(np.ravel(got) - np.ravel(want)).max() / max(np.abs(want).max(), 1e-300)
+    assert r <= tol and m <= 10 * tol, f"{what}: rel L2 {r:.3e}, max rel {m:.3e} (tol {tol:.1e})"
+
+
+def run_pair(lee, name, shape, tau, nsteps, storage="f64", bc="periodic", seed=0, sponge_w=0, smax=0.0,
+             fields=None):
+    s = oracle.velset(name)
+    cells = int(np.prod(shape))
+    rho, u, th = fields if fields is not None else inputs.random_fields(shape, s.D, seed)
+    kw = dict(sponge_width=sponge_w, sponge_strength=smax) if bc == "open_sponge" else {}
+    with lee.Solver(name, shape, tau, storage=storage, bc=bc, **kw) as sv:
+        sv.init_fields(rho, u, th)
+        sv.step(nsteps)
+        g_gpu = np.empty((s.q, cells))
+        sv.get_populations(g_gpu)
+        mr, mu, mt = np.empty(cells), np.empty((s.D, cells)), np.empty(cells)
+        sv.moments(mr, mu, mt)
+        red = np.empty(s.D + 4)
+        sv.reduce(red)
+    g0 = oracle.equilibrium(name, rho, u, th)
+    obc = bc if bc != "open_learned" else "open_zero"
+    g = oracle.step(name, shape, tau, g0, nsteps, bc=obc, sponge_w=sponge_w, sponge_smax=smax)
+    post = oracle.post_state(name, shape, tau, g, bc=obc, sponge_w=sponge_w, sponge_smax=smax)
+    p = perm_to_lib(lee, name)
+    return dict(g_gpu=g_gpu, g_ora=post[p], m_gpu=(mr, mu, mt), m_ora=oracle.moments(name, post), red_gpu=red,
+                red_ora=oracle.reduce(name, post))
+
+
+@pytest.mark.parametrize("name", SETS)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("vector", [True, False])
+def test_periodic_parity(gpu_lib, name, storage, vector):
+    s = oracle.velset(name)
+    for shape in shapes_for(s.D, vector):
+        for nsteps, tau in ((1, 0.6), (2, 0.5), (7, 0.83), (50, 0.55)):
+            r = run_pair(gpu_lib, name, shape, tau, nsteps, storage=storage, seed=nsteps)
+            tol = TOL[storage]
+            assert_close(r["g_gpu"], r["g_ora"], tol, f"{name} {storage} {shape} n={nsteps} populations")
+            for a, b, w in zip(r["m_gpu"], r["m_ora"], ("rho", "u", "theta")):
+                assert_close(a, b, tol * 10, f"{name} {storage} {shape} n={nsteps} {w}")
+
+
+@pytest.mark.parametrize("name", ["D1Q3", "D2Q5", "D2Q5_DI", "D3Q7", "D3Q19"])
+@pytest.mark.parametrize("bc", ["open_zero", "open_sponge"])
+def test_open_boundary_parity(gpu_lib, name, bc):
+    s = oracle.velset(name)
+    for vector in (True, False):
+        shape = shapes_for(s.D, vector)[0]
+        w = 3 if bc == "open_sponge" else 0
+        r = run_pair(gpu_lib, name, shape, 0.7, 9, storage="f64", bc=bc, seed=3, sponge_w=w, smax=0.4)
+        assert_close(r["g_gpu"], r["g_ora"], 1e-12, f"{name} {bc} {shape}")
+
+
+@pytest.mark.parametrize("name,storage", [("D3Q7", "f16"), ("D3Q7", "bf16"), ("D3Q7_DI", "f16"), ("D2Q5", "f16"),
+                                          ("D2Q5", "bf16"), ("D3Q19", "f16"), ("D3Q19", "bf16"), ("D1Q3", "bf16")])
+def test_16bit_storage_error_is_bounded(gpu_lib, name, storage):
+    s = oracle.velset(name)
+    shape = shapes_for(s.D, True)[0]
+    cells = int(np.prod(shape))
+    # a smooth pulse, the workload of the 16-bit configuration
+    c = [n / 2.3 for n in shape]
+    rho = inputs.gaussian_pulse(shape, 1e-3, 3.0, c)
+    u, th = inputs.zero_rest(s.D, cells)
+    n = 40
+    r = run_pair(gpu_lib, name, shape, 0.55, n, storage=storage, fields=(rho, u, th))
+    unit = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    bound = 4 * unit * np.sqrt(10 * n)
+    err = rel_l2(r["m_gpu"][0], r["m_ora"][0])
+    assert err <= bound, (err, bound)
+    assert err > 0
+
+
+@pytest.mark.parametrize("name", SETS)
+def test_reduction_matches_oracle_and_conserves(gpu_lib, name):
+    s = oracle.velset(name)
+    shape = shapes_for(s.D, True)[0]
+    r = run_pair(gpu_lib, name, shape, 0.6, 20, storage="f64", seed=9)
+    np.testing.assert_allclose(r["red_gpu"][:-1], r["red_ora"][:-1], rtol=1e-12, atol=1e-15)
+    assert r["red_gpu"][-1] == 0
+    # conservation against the initial state (periodic)
+    rho, u, th = inputs.random_fields(shape, s.D, 9)
+    g0 = oracle.equilibrium(name, rho, u, th)
+    r0 = oracle.reduce(name, g0)
+    scale = np.abs(g0).sum()
+    np.testing.assert_allclose(r["red_gpu"][: s.D + 2], r0[: s.D + 2], atol=1e-13 * scale)
+
+
+def test_checkpoint_resume_is_bitwise(gpu_lib):
+    lee = gpu_lib
+    name, shape = "D3Q19", (36, 10, 7)
+    s = oracle.velset(name)
+    cells = int(np.prod(shape))
+    rho, u, th = inputs.random_fields(shape, s.D, 4)
+    for storage in ("f64", "f32", "f16"):
+        with lee.Solver(name, shape, 0.6, storage=storage) as a:
+            a.init_fields(rho, u, th)
+            a.step(12)
+            full = np.empty((s.q, cells))
+            a.get_populations(full)
+        with lee.Solver(name, shape, 0.6, storage=storage, store_scale=0.0) as b:
+            b.init_fields(rho, u, th)
+            b.step(5)
+            ck = np.empty((s.q, cells))
+            b.get_populations(ck)
+            scale = b.store_scale
+        with lee.Solver(name, shape, 0.6, storage=storage, store_scale=scale if storage == "f16" else 0.0) as c:
+            c.set_populations(ck)
+            c.step(7)
+            resumed = np.empty((s.q, cells))
+            c.get_populations(resumed)
+        assert np.array_equal(full, resumed), storage
+
+
+def test_runs_are_bitwise_repeatable(gpu_lib):
+    lee = gpu_lib
+    shape = (256, 64, 1)
+    rho, u, th = inputs.config_2d(256, seed=2)
+    outs = []
+    for _ in range(2):
+        with lee.Solver("D2Q5", shape, 0.6, storage="f32") as sv:
+            sv.init_fields(rho, u, th)
+            sv.step(33)
+            g = np.empty((5, shape[0] * shape[1]))
+            sv.get_populations(g)
+            red = np.empty(6)
+            sv.reduce(red)
+            outs.append((g, red))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def eigenmode(name, shape, tau, m, lee):
+    """Post-collision eigenmode: S = Re(v e^{i k.x}) with v an eigenvector of H(tau) D(k), the
+    Fourier symbol of the pull step on post-collision states (Sec. 7 with the factors swapped).
+    Returns (lambda, v in library order, k)."""
+    s = oracle.velset(name)
+    k = 2 * np.pi * np.array(m, dtype=float) / np.array(shape)
+    k[s.D:] = 0.0
+    G = an.h_matrix(s, tau) @ np.diag(np.exp(-1j * (s.c.astype(float) @ k)))
+    lam, V = np.linalg.eig(G)
+    j = int(np.argmax(np.abs(lam)))  # a least-damped (acoustic) mode
+    return lam[j], V[:, j][perm_to_lib(lee, name)], k
+
+
+def mode_field(v, k, shape, amp, cells_idx=None):
+    """amp * Re(v e^{i k.x}) as [q][cells] (or only at the flat cell indices given)."""
+    nx, ny, nz = shape
+    if cells_idx is None:
+        cells_idx = np.arange(nx * ny * nz)
+    x = cells_idx % nx
+    y = (cells_idx // nx) % ny
+    z = cells_idx // (nx * ny)
+    ph = k[0] * x + k[1] * y + k[2] * z
+    c, sn = np.cos(ph), np.sin(ph)
+    out = np.empty((len(v), len(cells_idx)))
+    for i in range(len(v)):
+        out[i] = amp * (v[i].real * c - v[i].imag * sn)
+    return out
+
+
+@pytest.mark.parametrize("name,shape,storage,nsteps,tol", [
+    ("D2Q5", (2048, 2048, 1), "f64", 100, 1e-12),
+    ("D2Q5", (2048, 2048, 1), "f32", 1000, 2e-5),
+    ("D3Q7", (384, 384, 384), "f32", 500, 2e-5),
+    ("D3Q7", (384, 384, 384), "f64", 20, 1e-12),
+])
+def test_full_size_eigenmode_evolves_exactly(gpu_lib, name, shape, storage, nsteps, tol):
+    """At the benchmark sizes: a Fourier eigenmode of the step evolves by lambda^n, an exact
+    property the oracle's linear algebra gives at any size; compared element by element on all
+    cells (2D) or on 2^21 sampled cells (3D)."""
+    lee = gpu_lib
+    s = oracle.velset(name)
+    cells = int(np.prod(shape))
+    m = (3, 5, 2)[: s.D] + (0,) * (3 - s.D)
+    lam, v, k = eigenmode(name, shape, 0.6, m, lee)
+    with lee.Solver(name, shape, 0.6, storage=storage) as sv:
+        sv.set_populations(mode_field(v, k, shape, 1e-3))
+        sv.step(nsteps)
+        g = np.empty((s.q, cells))
+        sv.get_populations(g)
+    idx = None if cells <= 2 ** 23 else np.random.default_rng(0).choice(cells, 2 ** 21, replace=False)
+    want = mode_field(lam ** nsteps * v, k, shape, 1e-3, idx)
+    got = g if idx is None else g[:, idx]
+    assert_close(got, want, tol, f"{name} {shape} {storage} eigenmode")
+
+
+def test_full_size_2d_config_against_oracle(gpu_lib):
+    """The 2D configuration itself (D2Q5, 2048^2, tau = 0.6, pulse + 8 plane waves, 1000 steps)
+    in FP64 on the GPU against the oracle run on all host cores."""
+    import os
+
+    lee = gpu_lib
+    name, n = "D2Q5", 2048
+    shape = (n, n, 1)
+    rho, u, th = inputs.config_2d(n, seed=2)
+    with lee.Solver(name, shape, 0.6, storage="f64") as sv:
+        sv.init_fields(rho, u, th)
+        sv.step(1000)
+        mr = np.empty(n * n)
+        sv.moments(mr)
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        g = oracle.step(name, shape, 0.6, oracle.equilibrium(name, rho, u, th), 1000)
+    finally:
+        oracle.set_threads(1)
+    want = oracle.moments(name, g)[0]
+    assert_close(mr, want, 1e-12, "2D config rho'")
