@@ -1,0 +1,454 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the fused stream-collide step on GB300.
+
+Workload (one benchmark step = one pass of the whole hot path over one synthetic input):
+  2D periodic D2Q5 grid of 2048 x 2048 cells, FP32 storage and arithmetic, tau = 0.6, initial
+  field = Gaussian pulse (amplitude 1e-3, width 32 cells) + 8 density plane waves (amplitude
+  1e-4, wavelength 16-256 cells), seed 2;  init_fields (equilibrium of the fields) -> 1000 time
+  steps -> per-cell moments -> FP64 global sums.
+value   = cells * 1000 * K / (sum of the K device-timed steps), in MLUPS (10^6 lattice updates/s).
+e2e     = the same through the C ABI with pinned host buffers: fields copied in and moments copied
+          out inside the timed region.
+Extra forms (not part of the timed value): 3D D3Q7 384^3 with FP32/FP16/BF16 storage against the
+FP64 run (MLUPS and relative L2 of rho').
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
+With N > 1 (torchrun, one process per GPU) every rank runs an independent replica of the
+workload ("replicas only": the single-domain path has no exchange step on one box).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+NX = 2048
+NSTEPS = 1000
+TAU = 0.6
+SET = "D2Q5"
+STORAGE = "f32"
+BYTES_PER_LUP = 2 * 5 * 4  # read + write of q = 5 FP32 populations (algorithmic)
+L2_FLUSH_BYTES = 512 << 20
+WORKLOAD = "2D D2Q5 periodic 2048x2048, FP32, tau=0.6, pulse+8 plane waves, 1000 steps/job"
+PROFILE = os.path.join(ROOT, "profiles", "stream_collide_d2q5_f32_2048x2048.md")
+KERNEL_SOURCES = ["paper_1601_08103_gb300/csrc/kernels.cuh", "paper_1601_08103_gb300/csrc/set_impl.cuh",
+                  "paper_1601_08103_gb300/csrc/velsets.cuh"]
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per stream-collide launch from the committed ncu summary, or None if the
+    summary is missing or was taken on different kernel sources."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not sha or not tr or sha.group(1) != kernel_source_sha():
+        return None
+    return float(tr.group(1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = np.array([r[0] for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(ngpus: int):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Maximum of a per-rank float over all ranks (the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+    from paper_1601_08103_gb300 import inputs
+
+    lee.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cells = NX * NX
+    rho, u, th = inputs.config_2d(NX, seed=2)
+    rho_d = torch.from_numpy(rho).to(dev)
+    u_d = torch.from_numpy(u).to(dev)
+    th_d = torch.from_numpy(th).to(dev)
+    mom_d = torch.empty((4, cells), dtype=torch.float64, device=dev)
+    red_d = torch.empty(8, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sv = lee.Solver(SET, (NX, NX, 1), TAU, storage=STORAGE, stream=stream)
+
+    launches_per_step = 1 + NSTEPS + 1 + 2  # init, steps, moments, reduce (partial + final)
+
+    def one_step(ev):
+        ev[0].record(stream)
+        sv.init_fields(rho_d, u_d, th_d)
+        ev[1].record(stream)
+        sv.step(NSTEPS)
+        ev[2].record(stream)
+        sv.moments(mom_d[0], mom_d[1:3], mom_d[3])
+        sv.reduce(red_d)
+        ev[3].record(stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    warm = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step(warm)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # untimed L2 flush between timed steps
+        one_step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [evs[k][0].elapsed_time(evs[k][3]) for k in range(args.steps)]
+    loop_ms = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    kernel_avg_s = float(np.mean(loop_ms)) / 1e3 / NSTEPS
+    value = world * cells * NSTEPS * args.steps / (total_ms / 1e3) / 1e6
+
+    # sanity: finite and conserved
+    red = red_d.cpu().numpy()
+    if not np.isfinite(red[:5]).all() or red[5] != 0:
+        raise RuntimeError(f"benchmark state not finite: {red}")
+
+    # end-to-end through the C ABI with pinned host buffers
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    th_h = torch.from_numpy(th).pin_memory()
+    out_h = torch.empty((4, cells), dtype=torch.float64).pin_memory()
+    red_h = np.empty(8)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sv.init_fields(rho_h, u_h, th_h)
+        sv.step(NSTEPS)
+        sv.moments(out_h[0], out_h[1:3], out_h[3])
+        sv.reduce(red_h)
+        t2 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t2 - t1)
+    e2e_total = max_over_ranks(sum(e2e_times), world)
+    e2e_value = world * cells * NSTEPS * args.steps / e2e_total / 1e6
+    h2d = rho.nbytes + u.nbytes + th.nbytes
+    d2h = out_h.numel() * 8 + 6 * 8
+
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_LUP * cells / kernel_avg_s / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline",
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "lbm_steps_per_job": NSTEPS, "velset": SET, "tau": TAU,
+                   "storage": STORAGE, "parallelism": f"replicas{world}",
+                   "l2": "512 MiB write between timed steps; ping-pong working set 168 MB > 129 MB L2",
+                   "wall_s_timed_region": round(wall, 3)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_stream_collide<D2Q5,float,V=4,periodic>",
+                     "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
+                     "avg_launch_us": round(kernel_avg_s * 1e6, 3)},
+        "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    sv.close()
+    return line
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of the workload:
+    the full 2048^2 grid for as many steps as fit in about budget_s seconds."""
+    import oracle
+    from paper_1601_08103_gb300 import inputs
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    rho, u, th = inputs.config_2d(NX, seed=2)
+    g = oracle.equilibrium(SET, rho, u, th)
+    t0 = time.perf_counter()
+    g = oracle.step(SET, (NX, NX, 1), TAU, g, 2)
+    probe = time.perf_counter() - t0
+    n = int(max(2, min(200, budget_s / max(probe / 2, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(SET, (NX, NX, 1), TAU, g, n)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return {"value": round(NX * NX * n / dt / 1e6, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{NX}x{NX} D2Q5 FP64, {n} steps, {cores} OpenMP threads, {dt:.1f} s"}
+
+
+def forms_3d():
+    """Mixed-precision storage forms on the 3D configuration (D3Q7, 384^3, tau = 0.55, Gaussian
+    pulse amplitude 1e-3 width 16, 500 steps): MLUPS of each storage and relative L2 of rho'
+    against the FP64 run on the same GPU (FP64 itself is held to the oracle by the tests)."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+    from paper_1601_08103_gb300 import inputs
+
+    n, steps = 384, 500
+    cells = n ** 3
+    rho, u, th = inputs.config_3d(n, seed=3)
+    dev = torch.device("cuda")
+    rho_d, u_d, th_d = (torch.from_numpy(a).to(dev) for a in (rho, u, th))
+    out = {}
+    ref = None
+    stream = torch.cuda.current_stream()
+    for storage in ("f64", "f32", "f16", "bf16"):
+        with lee.Solver("D3Q7", (n, n, n), 0.55, storage=storage, stream=stream) as sv:
+            sv.init_fields(rho_d, u_d, th_d)
+            sv.step(2)
+            sv.init_fields(rho_d, u_d, th_d)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sv.step(steps)
+            e1.record(stream)
+            r = torch.empty(cells, dtype=torch.float64, device=dev)
+            sv.moments(r, None, None)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        if storage == "f64":
+            ref = r
+        err = float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))
+        bpl = 2 * 7 * lee.STORAGE_BYTES[storage]
+        out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
+                        "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "rel_l2_rho_vs_f64": err}
+    return {"workload": "3D D3Q7 periodic 384^3, tau=0.55, pulse A=1e-3 w=16, 500 steps", "storage": out}
+
+
+CASES = {
+    # name: (set, shape, storage, tau)
+    "d1q3_f64": ("D1Q3", (1024, 1, 1), "f64", 0.8),
+    "d2q5_f32": ("D2Q5", (2048, 2048, 1), "f32", 0.6),
+    "d2q5_f64": ("D2Q5", (2048, 2048, 1), "f64", 0.6),
+    "d3q7_f32": ("D3Q7", (384, 384, 384), "f32", 0.55),
+    "d3q7_f64": ("D3Q7", (384, 384, 384), "f64", 0.55),
+    "d3q7_f16": ("D3Q7", (384, 384, 384), "f16", 0.55),
+    "d3q7_bf16": ("D3Q7", (384, 384, 384), "bf16", 0.55),
+    "d3q19_f32": ("D3Q19", (256, 256, 256), "f32", 0.55),
+}
+
+
+def run_case(args):
+    """One configuration alone (for profiling): warmup LBM steps, then --steps LBM steps timed
+    with CUDA events; prints a small JSON line (not a benchmark line)."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+    from paper_1601_08103_gb300 import inputs
+
+    name, shape, storage, tau = CASES[args.case]
+    lee.load()
+    stream = torch.cuda.current_stream()
+    D = lee.lee_velset_info(name)["D"]
+    cells = int(np.prod(shape))
+    c = [n / 2.7 for n in shape]
+    rho = inputs.gaussian_pulse(shape, 1e-3, 16.0, c)
+    u, th = inputs.zero_rest(D, cells)
+    with lee.Solver(name, shape, tau, storage=storage, stream=stream) as sv:
+        sv.init_fields(rho, u, th)
+        sv.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sv.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ok = sv.check_finite()
+    q = lee.lee_velset_info(name)["q"]
+    bpl = 2 * q * lee.STORAGE_BYTES[storage]
+    print(json.dumps({"case": args.case, "cells": cells, "steps": args.steps, "ms": ms, "finite": ok,
+                      "mlups": cells * args.steps / (ms / 1e3) / 1e6,
+                      "gbs": bpl * cells * args.steps / (ms / 1e3) / 1e9}), flush=True)
+    return 0 if ok else 1
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1601_08103_gb300 import inputs
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    rho, u, th = inputs.config_2d(NX, seed=2)
+    g0 = oracle.equilibrium(SET, rho, u, th)
+    sample_steps = 3
+    for _ in range(args.warmup):
+        oracle.step(SET, (NX, NX, 1), TAU, g0, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(SET, (NX, NX, 1), TAU, g0, sample_steps)
+    dt = time.perf_counter() - t0
+    value = NX * NX * sample_steps * args.steps / dt / 1e6
+    sample = f"{NX}x{NX} D2Q5 FP64, {sample_steps} steps per timed step, {cores} OpenMP threads"
+    return {"impl": "reference", "metric": "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline",
+            "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": NX * NX, "velset": SET, "tau": TAU,
+                       "note": "oracle: plain FP64 C restatement of the paper's update, bounded sample"},
+            "cpu_baseline": {"value": round(value, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 2), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=sorted(CASES), help="time one configuration alone (profiling)")
+    args = ap.parse_args(argv)
+    if args.case:
+        return run_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        if world == 1 and not args.no_forms:
+            line["forms"] = forms_3d()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -18,7 +18,8 @@
  *  - State: the device buffer holds the POST-collision populations of the current time t,
  *    g*(t) = (1 - 1/tau) g(t) + (1/tau) g^eq(g(t)) (then damped inside a sponge frame); the next
  *    step pulls g_i(t+1, x) = g*_i(t, x - c_i) and collides it.  Right after init_fields,
- *    g*(0) = g(0) = g^eq(IC) (Sec. 7 initial condition), which is its own collision.
+ *    g*(0) = g(0) = g^eq(IC) (Sec. 7 initial condition), which is its own collision (times the
+ *    frame damping inside a sponge frame).
  *  - Collision keeps rho', u' and theta' of every cell, so moments of g*(t) are those of g(t)
  *    (except inside a sponge frame, where they include that step's damping).
  *  - Ownership: the handle owns all device memory it allocates; caller buffers are only read or

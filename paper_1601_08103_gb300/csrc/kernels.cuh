@@ -409,6 +409,27 @@ __global__ void k_init_maxabs(const double *__restrict__ rho, const double *__re
     if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(m));
 }
 
+// Sponge damping of a stored post-collision state: g* <- (1 - sigma(d)) g* in the frame cells.
+// Applied once after init_fields so that the initial state is a post-collision state like every
+// later one (the equilibrium is its own collision; the frame damping is not).
+template <class S, class T>
+__global__ void k_sponge_damp(T *__restrict__ g, GridDesc gd, int w, typename Store<T>::C smax) {
+    using C = typename Store<T>::C;
+    const long long cells = (long long)gd.nx * gd.ny * gd.nz;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(x % gd.nx);
+        const long long r = x / gd.nx;
+        const int cy = (int)(r % gd.ny), cz = (int)(r / gd.ny);
+        const C damp = sponge_factor<C>(cx, cy, cz, gd, S::D, w, smax);
+        if (damp == C(1)) continue;
+#pragma unroll
+        for (int i = 0; i < S::Q; ++i) {
+            T *p = g + (long long)i * gd.pitch + x;
+            *p = Store<T>::make(Store<T>::load(*p) * damp);
+        }
+    }
+}
+
 // Per-cell moments (Sec. 4 discrete moments, Sec. 5 temperature) in FP64.
 template <class S, class T>
 __global__ void k_moments(const T *__restrict__ g, long long cells, long long pitch, SetConsts k, double *__restrict__ rho,

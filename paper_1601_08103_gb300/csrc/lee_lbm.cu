@@ -307,6 +307,10 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
     }
     const SetConsts k = consts_for(h->cfg.set, h->scale);
     LEE_CK(h, h->ops->init(h->cfg.storage, dr, du, dt, h->buf[0], h->cells, h->pitch, k, h->st), "init kernel");
+    if (h->cfg.bc == LEE_BC_OPEN_SPONGE)
+        LEE_CK(h, h->ops->sponge_damp(h->cfg.storage, h->buf[0], (int)h->cfg.nx, (int)h->cfg.ny, (int)h->cfg.nz, h->pitch,
+                                      h->cfg.sponge_width, h->cfg.sponge_strength, h->st),
+               "sponge damp");
     h->cur = 0;
     h->steps = 0;
     if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");

@@ -48,6 +48,9 @@ struct SetOps {
                               cudaStream_t st);
     cudaError_t (*import_f64)(int storage, const double *in, long long cells, long long pitch, const SetConsts &k, void *g,
                               cudaStream_t st);
+    // sponge-frame damping of a stored state (after init_fields)
+    cudaError_t (*sponge_damp)(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
+                               cudaStream_t st);
     // description for lee_velset_info
     int c[27][3];
     int shell[27];

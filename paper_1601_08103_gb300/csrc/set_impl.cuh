@@ -116,6 +116,16 @@ struct SetImpl {
             return cudaGetLastError();
         });
     }
+    static cudaError_t sponge_damp(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
+                                   cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            using C = typename Store<T>::C;
+            GridDesc gd{nx, ny, nz, nx, (long long)nx * ny * nz, pitch};
+            k_sponge_damp<S, T><<<aux_blocks(gd.nchunks), 256, 0, st>>>(static_cast<T *>(g), gd, w, (C)smax);
+            return cudaGetLastError();
+        });
+    }
     static SetOps make() {
         SetOps o{};
         o.D = S::D;
@@ -127,6 +137,7 @@ struct SetImpl {
         o.reduce_partial = &reduce_partial;
         o.export_f64 = &export_f64;
         o.import_f64 = &import_f64;
+        o.sponge_damp = &sponge_damp;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);
