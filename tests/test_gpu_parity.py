@@ -37,7 +37,7 @@ def shapes_for(D, vector=True):
         return [(1024, 1, 1)] if vector else [(1027, 1, 1)]
     if D == 2:
         return [(260, 37, 1)] if vector else [(129, 33, 1)]
-    return [(36, 10, 7)] if vector else [(13, 11, 3)]
+    return [(36, 10, 7)] if vector else [(13, 11, 9)]
 
 
 def rel_l2(a, b):
