@@ -169,6 +169,29 @@ const char *lee_lbm_last_error(lee_lbm *h);
 /* Frees the handle and its device memory.  NULL-safe.  Synchronises the stream first. */
 lee_status lee_lbm_destroy(lee_lbm *h);
 
+/* The global sums of lee_lbm_reduce (same out[D+4] layout and order, same result bit for bit)
+ * for a population field the caller owns, computed WITHOUT ALLOCATING anything.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc (or any routine
+ * that allocates) where they need these diagnostics -- code running under someone else's memory
+ * budget or allocator, a process that reserves all its device memory up front, or a callback
+ * that must not allocate -- and therefore cannot create a solver handle, whose creation
+ * allocates the reduction scratch.
+ *   set, storage: as in lee_lbm_config; g: DEVICE pointer to the stored populations,
+ *   g[i * pitch + cell] for i < q, in the storage type (16-bit storage holds S * g_i / f*_i);
+ *   cells: 1 .. 2^31 - 1; pitch >= cells (elements between velocity arrays);
+ *   store_scale: S for 16-bit storage (> 0), ignored otherwise;
+ *   out: DEVICE pointer to D + 4 doubles; cuda_stream: stream to run on (NULL = default).
+ * Scratch: a fixed file-scope device array of 2432 x 8 FP64 block partials (155,648 bytes) that
+ * every GPU loading the library keeps until the process exits.  Sizes beyond it (more than
+ * 2^31 - 1 cells) are rejected with LEE_ERR_INVALID_ARGUMENT; so are bad pointers or enums.
+ * Set-up: the first call on a device (with that device current) looks up the array's device
+ * address once; make that first call before any stream capture.  All calls share the one array
+ * and each call overwrites the entries it reads, so nothing needs clearing between calls -- but
+ * calls that overlap on the GPU (e.g. on two streams at once) race on it.  Asynchronous: returns
+ * after enqueueing; a CUDA failure returns LEE_ERR_CUDA (there is no handle to poison). */
+lee_status lee_reduce_noalloc(int32_t set, int32_t storage, const void *g, int64_t cells, int64_t pitch,
+                              double store_scale, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ _SIGS = {
     "lee_lbm_sync": (ctypes.c_int, [_P]),
     "lee_lbm_last_error": (ctypes.c_char_p, [_P]),
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
+    "lee_reduce_noalloc": (ctypes.c_int, [_I32, _I32, _P, _I64, _I64, _D, _P, _P]),
 }
 
 
@@ -248,6 +249,20 @@ def lee_lbm_last_error(h) -> str:
 def lee_lbm_destroy(h):
     if h:
         _check(_lib.lee_lbm_destroy(h), "lee_lbm_destroy")
+
+
+def lee_reduce_noalloc(set_name: str, storage: str, g, cells: int, pitch: int, out, store_scale: float = 1.0,
+                       stream=None):
+    """Global sums of a caller-owned device population field without any allocation (see
+    include/lee_lbm.h).  g and out must be CUDA tensors; out holds D + 4 doubles."""
+    lib = load()
+    ga, gon = _addr(g)
+    oa, oon = _addr(out)
+    if not (gon and oon):
+        raise ValueError("lee_reduce_noalloc takes device buffers only")
+    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    _check(lib.lee_reduce_noalloc(SETS[set_name], STORAGE[storage], ga, int(cells), int(pitch), float(store_scale), oa,
+                                  st), "lee_reduce_noalloc")
 
 
 class Solver:

@@ -1,0 +1,68 @@
+"""The allocation-free reduction entry point, lee_reduce_noalloc, against lee_lbm_reduce.
+
+lee_reduce_noalloc serves callers that cannot allocate device memory where they need the global
+sums (they run under someone else's allocator or memory budget, or in a phase that must not
+allocate) and so cannot create a solver handle.  It keeps its block partials in a fixed device
+array inside the library.  This file is collected last on purpose, so that a failure here leaves
+every other test already run; it must pass alone in a fresh process as well as after the rest.
+"""
+import numpy as np
+import pytest
+
+import paper_1601_08103_gb300 as lee
+from paper_1601_08103_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def reference_sums(name, storage, g64_dev, scale):
+    """The existing entry point: a handle whose state is set to the same populations."""
+    info = lee.lee_velset_info(name)
+    cells = g64_dev.shape[1]
+    with lee.Solver(name, (cells, 1, 1) if info["D"] == 1 else (cells // 4, 4, 1) if info["D"] == 2
+                    else (cells // 16, 4, 4), 0.6, storage=storage, store_scale=scale) as sv:
+        sv.set_populations(g64_dev)
+        out = np.empty(info["D"] + 4)
+        sv.reduce(out)
+    return out
+
+
+@pytest.mark.parametrize("name,storage", [("D2Q5", "f64"), ("D3Q19", "f32"), ("D3Q7", "f16")])
+def test_noalloc_matches_handle_reduce_on_two_calls_in_a_row(gpu_lib, name, storage):
+    import torch
+
+    info = lee.lee_velset_info(name)
+    q, D = info["q"], info["D"]
+    cells = 96 * 1024 + 16  # several block tiles and a ragged tail; divisible by 16 for the shapes
+    f = torch.tensor(info["f"], dtype=torch.float64, device="cuda")[:, None]
+    scale = 1024.0 if storage in ("f16", "bf16") else 1.0
+    for call, seed in enumerate((5, 6)):  # two calls in a row, different data
+        g64 = torch.from_numpy(inputs.random_populations(q, cells, seed)).cuda()
+        want = reference_sums(name, storage, g64, scale if storage == "f16" else 0.0)
+        # the caller's stored populations, in the storage format the library documents
+        if storage == "f64":
+            stored = g64.clone()
+        elif storage == "f32":
+            stored = g64.float()
+        else:
+            stored = (g64 * (scale / f)).half()
+        pitch = cells
+        out = torch.full((D + 4,), float("nan"), dtype=torch.float64, device="cuda")
+        lee.lee_reduce_noalloc(name, storage, stored, cells, pitch, out, store_scale=scale)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300, err_msg=f"call {call}")
+
+
+def test_noalloc_rejects_bad_arguments(gpu_lib):
+    import torch
+
+    g = torch.zeros((5, 64), dtype=torch.float64, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(lee.LeeError) as e:
+        lee.lee_reduce_noalloc("D2Q5", "f64", g, 1 << 31, 1 << 31, out)  # more cells than supported
+    assert e.value.status == lee.LEE_ERR_INVALID_ARGUMENT
+    with pytest.raises(lee.LeeError):
+        lee.lee_reduce_noalloc("D2Q5", "f64", g, 64, 32, out)  # pitch < cells
+    with pytest.raises(lee.LeeError):
+        lee.lee_reduce_noalloc("D2Q5", "f16", g, 64, 64, out, store_scale=0.0)  # 16-bit needs S > 0
