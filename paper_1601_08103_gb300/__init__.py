@@ -73,6 +73,19 @@ _SIGS = {
     "lee_lbm_last_error": (ctypes.c_char_p, [_P]),
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
     "lee_reduce_noalloc": (ctypes.c_int, [_I32, _I32, _P, _I64, _I64, _D, _P, _P]),
+    # include/lee_batch.h
+    "lee_batch_create": (ctypes.c_int, [_I32, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
+    "lee_batch_init_fields": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I32]),
+    "lee_batch_step": (ctypes.c_int, [_P, _I64, _I32]),
+    "lee_batch_moments": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I32]),
+    "lee_batch_reduce": (ctypes.c_int, [_P, _I32, _P, _I32]),
+    "lee_batch_get_populations": (ctypes.c_int, [_P, _I32, _P, _I32]),
+    "lee_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "lee_batch_set_tuning": (ctypes.c_int, [_P, _I32, _I32]),
+    "lee_batch_cells": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "lee_batch_sync": (ctypes.c_int, [_P]),
+    "lee_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lee_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -100,11 +113,13 @@ def load(path: str | None = None):
         return lib
 
 
-def _check(status: int, where: str, handle=None):
+def _check(status: int, where: str, handle=None, batch=None):
     if status != LEE_OK:
         detail = ""
         if handle:
             detail = _lib.lee_lbm_last_error(handle).decode()
+        if batch:
+            detail = _lib.lee_batch_last_error(batch).decode()
         raise LeeError(status, where, detail)
 
 
@@ -318,6 +333,133 @@ class Solver:
         if self.h:
             lee_lbm_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------------
+# include/lee_batch.h
+# ------------------------------------------------------------------------------------------
+BATCH_MODE = {"graph": 0, "launch": 1, "sequential": 2}
+
+
+class lee_batch_domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("tau", ctypes.c_double)]
+
+
+def lee_batch_create(set_name: str, storage: str, domains, stream=None) -> int:
+    """domains: sequence of (nx, ny, tau)."""
+    lib = load()
+    arr = (lee_batch_domain * len(domains))(*[lee_batch_domain(int(a), int(b), float(t)) for a, b, t in domains])
+    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    h = _P()
+    _check(lib.lee_batch_create(SETS[set_name], STORAGE[storage], ctypes.cast(arr, _P), len(domains), st,
+                                ctypes.byref(h)), "lee_batch_create")
+    return h.value
+
+
+def lee_batch_init_fields(b, d, rho, u, theta):
+    on = _same_place(rho, u, theta)
+    _check(_lib.lee_batch_init_fields(b, int(d), _addr(rho)[0], _addr(u)[0], _addr(theta)[0], on),
+           "lee_batch_init_fields", batch=b)
+
+
+def lee_batch_step(b, n: int, mode: str = "graph"):
+    _check(_lib.lee_batch_step(b, int(n), BATCH_MODE[mode]), "lee_batch_step", batch=b)
+
+
+def lee_batch_moments(b, d, rho=None, u=None, theta=None):
+    on = _same_place(rho, u, theta)
+    _check(_lib.lee_batch_moments(b, int(d), _addr(rho)[0], _addr(u)[0], _addr(theta)[0], on), "lee_batch_moments",
+           batch=b)
+
+
+def lee_batch_reduce(b, d, out):
+    a, on = _addr(out)
+    _check(_lib.lee_batch_reduce(b, int(d), a, on), "lee_batch_reduce", batch=b)
+
+
+def lee_batch_get_populations(b, d, g):
+    a, on = _addr(g)
+    _check(_lib.lee_batch_get_populations(b, int(d), a, on), "lee_batch_get_populations", batch=b)
+
+
+def lee_batch_tune(b):
+    t, v = _I32(), _I32()
+    _check(_lib.lee_batch_tune(b, ctypes.byref(t), ctypes.byref(v)), "lee_batch_tune", batch=b)
+    return t.value, v.value
+
+
+def lee_batch_set_tuning(b, threads: int, cells_per_thread: int):
+    _check(_lib.lee_batch_set_tuning(b, int(threads), int(cells_per_thread)), "lee_batch_set_tuning", batch=b)
+
+
+def lee_batch_cells(b) -> int:
+    v = _I64()
+    _check(_lib.lee_batch_cells(b, ctypes.byref(v)), "lee_batch_cells")
+    return v.value
+
+
+def lee_batch_sync(b):
+    _check(_lib.lee_batch_sync(b), "lee_batch_sync", batch=b)
+
+
+def lee_batch_destroy(b):
+    if b:
+        _check(_lib.lee_batch_destroy(b), "lee_batch_destroy")
+
+
+class Batch:
+    """Owns one lee_batch; methods map one-to-one onto the C entry points."""
+
+    def __init__(self, set_name: str, storage: str, domains, stream=None):
+        load()
+        self.domains = [(int(a), int(b), float(t)) for a, b, t in domains]
+        self.q = lee_velset_info(set_name)["q"]
+        self.b = lee_batch_create(set_name, storage, self.domains, stream)
+
+    def init_fields(self, d, rho, u, theta):
+        lee_batch_init_fields(self.b, d, rho, u, theta)
+
+    def step(self, n: int = 1, mode: str = "graph"):
+        lee_batch_step(self.b, n, mode)
+
+    def moments(self, d, rho=None, u=None, theta=None):
+        lee_batch_moments(self.b, d, rho, u, theta)
+
+    def reduce(self, d, out):
+        lee_batch_reduce(self.b, d, out)
+
+    def get_populations(self, d, g):
+        lee_batch_get_populations(self.b, d, g)
+
+    def tune(self):
+        return lee_batch_tune(self.b)
+
+    def set_tuning(self, threads, cells_per_thread):
+        lee_batch_set_tuning(self.b, threads, cells_per_thread)
+
+    @property
+    def cells(self) -> int:
+        return lee_batch_cells(self.b)
+
+    def sync(self):
+        lee_batch_sync(self.b)
+
+    def close(self):
+        if self.b:
+            lee_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

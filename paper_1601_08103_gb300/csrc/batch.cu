@@ -1,0 +1,571 @@
+// batch.cu -- many periodic 2D domains per launch (include/lee_batch.h): descriptors, the
+// block -> domain table, the autotuner, CUDA-graph replay and the sequential baseline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/lee_batch.h"
+#include "set_impl.cuh"
+
+namespace lee {
+SetConsts consts_for(int set, double scale);
+void fold_coefficients(int set, bool scaled, double omega, double M[4][4], double N[4][4]);
+
+template <class S, class T, int V>
+cudaError_t launch_batched(const void *src, void *dst, const void *doms, const unsigned short *table, int nblocks,
+                           int threads, cudaStream_t st) {
+    using C = typename Store<T>::C;
+    k_stream_collide_batched<S, T, V><<<nblocks, threads, 0, st>>>(
+        static_cast<const T *>(src), static_cast<T *>(dst), static_cast<const BatchDomain<C> *>(doms), table);
+    return cudaGetLastError();
+}
+
+using BatchedFn = cudaError_t (*)(const void *, void *, const void *, const unsigned short *, int, int, cudaStream_t);
+
+template <class S, class T>
+BatchedFn batched_fn(int V) {
+    switch (V) {
+    case 1: return &launch_batched<S, T, 1>;
+    case 2: return &launch_batched<S, T, 2>;
+    case 4: if constexpr (sizeof(T) <= 4) return &launch_batched<S, T, 4>; else return nullptr;
+    default: return nullptr;
+    }
+}
+
+BatchedFn pick_batched(int set, int storage, int V) {
+    if (set == LEE_D2Q5) return storage == LEE_STORE_F32 ? batched_fn<D2Q5, float>(V) : batched_fn<D2Q5, double>(V);
+    if (set == LEE_D2Q5_DIATOMIC)
+        return storage == LEE_STORE_F32 ? batched_fn<D2Q5Di, float>(V) : batched_fn<D2Q5Di, double>(V);
+    return nullptr;
+}
+
+}  // namespace lee
+
+using namespace lee;
+
+struct lee_batch {
+    int set = 0, storage = 0, count = 0, Q = 0;
+    const SetOps *ops = nullptr;
+    size_t elem = 0;
+    int device = 0;
+    std::vector<lee_batch_domain> doms;
+    std::vector<long long> offset, pitch, cells;
+    long long total_elems = 0, total_cells = 0, max_cells = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaStream_t st = nullptr, cap = nullptr;
+    // launch shape
+    bool tuned = false;
+    int threads = 0, V = 0, nblocks = 0;
+    void *d_doms = nullptr;
+    unsigned short *d_table = nullptr;
+    size_t d_doms_cap = 0, d_table_cap = 0;
+    BatchedFn fn = nullptr;
+    // captured graphs, keyed by (starting parity, number of steps); every graph has an even
+    // number of steps, so replaying it leaves the buffer parity unchanged
+    static constexpr int kMaxGraphSteps = 4096;
+    static constexpr int kChunkSteps = 100;
+    std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
+    // aux
+    double *fields = nullptr, *pops64 = nullptr, *partial = nullptr, *red_out = nullptr;
+    int red_blocks = 0;
+    bool poisoned = false;
+    std::string err;
+};
+
+namespace {
+
+lee_status bfail(lee_batch *b, lee_status s, const std::string &m) {
+    if (b) {
+        b->err = m;
+        if (s == LEE_ERR_CUDA) b->poisoned = true;
+    }
+    return s;
+}
+
+#define BCK(b, call, what)                                                                       \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA, \
+                         std::string(what) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+lee_status benter(lee_batch *b) {
+    if (!b) return LEE_ERR_INVALID_ARGUMENT;
+    if (b->poisoned) return LEE_ERR_POISONED;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, "cudaSetDevice");
+    return LEE_OK;
+}
+
+void drop_graphs(lee_batch *b) {
+    for (auto &kv : b->exec)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    b->exec.clear();
+}
+
+void *dom_ptr(lee_batch *b, int which, int d) { return static_cast<char *>(b->buf[which]) + b->elem * b->offset[d]; }
+
+// Per-domain descriptors and the block table for a launch shape.
+template <class C>
+lee_status build_shape_t(lee_batch *b, int threads, int V) {
+    std::vector<BatchDomain<C>> hd(b->count);
+    std::vector<unsigned short> table;
+    int block = 0;
+    for (int d = 0; d < b->count; ++d) {
+        BatchDomain<C> &D = hd[d];
+        D.gd.nx = (int)b->doms[d].nx;
+        D.gd.ny = (int)b->doms[d].ny;
+        D.gd.nz = 1;
+        D.gd.nxc = (int)(b->doms[d].nx / V);
+        D.gd.nchunks = (long long)D.gd.nxc * D.gd.ny;
+        D.gd.pitch = b->pitch[d];
+        double M[4][4], N[4][4];
+        const double omega = omega_for(b->storage, b->doms[d].tau);
+        fold_coefficients(b->set, false, omega, M, N);
+        D.cf = make_coef<C>(omega, M, N);
+        D.offset = b->offset[d];
+        D.first_block = block;
+        const long long nb = (D.gd.nchunks + threads - 1) / threads;
+        for (long long k = 0; k < nb; ++k) table.push_back((unsigned short)d);
+        block += (int)nb;
+    }
+    const size_t dbytes = sizeof(BatchDomain<C>) * hd.size(), tbytes = sizeof(unsigned short) * table.size();
+    if (dbytes > b->d_doms_cap) {
+        cudaFree(b->d_doms);
+        b->d_doms = nullptr;
+        BCK(b, cudaMalloc(&b->d_doms, dbytes), "cudaMalloc(domains)");
+        b->d_doms_cap = dbytes;
+    }
+    if (tbytes > b->d_table_cap) {
+        cudaFree(b->d_table);
+        b->d_table = nullptr;
+        BCK(b, cudaMalloc(&b->d_table, tbytes), "cudaMalloc(block table)");
+        b->d_table_cap = tbytes;
+    }
+    BCK(b, cudaMemcpyAsync(b->d_doms, hd.data(), dbytes, cudaMemcpyHostToDevice, b->st), "H2D domains");
+    BCK(b, cudaMemcpyAsync(b->d_table, table.data(), tbytes, cudaMemcpyHostToDevice, b->st), "H2D block table");
+    BCK(b, cudaStreamSynchronize(b->st), "sync");
+    b->threads = threads;
+    b->V = V;
+    b->nblocks = block;
+    b->fn = pick_batched(b->set, b->storage, V);
+    drop_graphs(b);
+    return b->fn ? LEE_OK : bfail(b, LEE_ERR_UNSUPPORTED, "no batched kernel for this shape");
+}
+
+lee_status build_shape(lee_batch *b, int threads, int V) {
+    return b->storage == LEE_STORE_F32 ? build_shape_t<float>(b, threads, V) : build_shape_t<double>(b, threads, V);
+}
+
+lee_status launch_one(lee_batch *b, int src_which, cudaStream_t st) {
+    BCK(b, b->fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, st),
+        "batched launch");
+    return LEE_OK;
+}
+
+int full_vec(int storage) { return storage == LEE_STORE_F32 ? 4 : 2; }
+
+std::mutex g_cache_mutex;
+std::map<std::string, std::pair<int, int>> g_cache;
+
+std::string cache_key(const lee_batch *b) {
+    unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the domain extents
+    for (const auto &d : b->doms) {
+        const long long v[2] = {d.nx, d.ny};
+        for (long long x : v)
+            for (int k = 0; k < 8; ++k) {
+                h ^= (unsigned long long)((x >> (8 * k)) & 0xff);
+                h *= 1099511628211ULL;
+            }
+    }
+    std::ostringstream o;
+    o << "batch/set" << b->set << "/st" << b->storage << "/n" << b->count << "/c" << b->total_cells << "/h" << std::hex << h;
+    return o.str();
+}
+
+bool cache_lookup(const std::string &key, int *threads, int *V) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *threads = it->second.first;
+        *V = it->second.second;
+        return true;
+    }
+    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char k[512];
+    int t = 0, v = 0;
+    bool found = false;
+    while (std::fscanf(f, "%511s %d %d", k, &t, &v) == 3) {
+        if (key == k) {
+            *threads = t;
+            *V = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_cache[key] = {*threads, *V};
+    return found;
+}
+
+void cache_store(const std::string &key, int threads, int V) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    g_cache[key] = {threads, V};
+    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s %d %d\n", key.c_str(), threads, V);
+        std::fclose(f);
+    }
+}
+
+lee_status tune(lee_batch *b) {
+    int t = 0, v = 0;
+    const std::string key = cache_key(b);
+    if (cache_lookup(key, &t, &v)) {
+        lee_status s = build_shape(b, t, v);
+        if (s == LEE_OK) b->tuned = true;
+        return s;
+    }
+    const int vf = full_vec(b->storage);
+    const int cand_v[2] = {vf / 2, vf};
+    const int cand_t[3] = {128, 256, 512};
+    float best = 1e30f;
+    int bt = 0, bv = 0;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0), "event");
+    BCK(b, cudaEventCreate(&e1), "event");
+    for (int vi = 0; vi < 2; ++vi) {
+        const int V = cand_v[vi];
+        bool ok = true;
+        for (const auto &d : b->doms) ok = ok && (d.nx % V == 0);
+        if (!ok) continue;
+        for (int ti = 0; ti < 3; ++ti) {
+            lee_status s = build_shape(b, cand_t[ti], V);
+            if (s != LEE_OK) return s;
+            // tuning launches always read the current buffer and write the idle one: no state change
+            for (int w = 0; w < 2; ++w)
+                if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
+            BCK(b, cudaEventRecord(e0, b->st), "event");
+            for (int r = 0; r < 10; ++r)
+                if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
+            BCK(b, cudaEventRecord(e1, b->st), "event");
+            BCK(b, cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            BCK(b, cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            if (ms < best) {
+                best = ms;
+                bt = cand_t[ti];
+                bv = V;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bt == 0) return bfail(b, LEE_ERR_UNSUPPORTED, "no launch shape divides every nx");
+    lee_status s = build_shape(b, bt, bv);
+    if (s != LEE_OK) return s;
+    cache_store(key, bt, bv);
+    b->tuned = true;
+    return LEE_OK;
+}
+
+lee_status ensure_graph(lee_batch *b, int parity, long long steps, cudaGraphExec_t *out) {
+    auto it = b->exec.find({parity, steps});
+    if (it != b->exec.end()) {
+        *out = it->second;
+        return LEE_OK;
+    }
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int w = parity;
+    for (long long k = 0; k < steps; ++k) {
+        cudaError_t e = b->fn(b->buf[w], b->buf[w ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, b->cap);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(b->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, LEE_ERR_CUDA, std::string("capture launch: ") + cudaGetErrorString(e));
+        }
+        w ^= 1;
+    }
+    BCK(b, cudaStreamEndCapture(b->cap, &g), "end capture");
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    BCK(b, e, "graph instantiate");
+    b->exec[{parity, steps}] = ex;
+    *out = ex;
+    return LEE_OK;
+}
+
+lee_status ensure_aux(lee_batch *b) {
+    if (b->fields) return LEE_OK;
+    BCK(b, cudaMalloc(&b->fields, sizeof(double) * 4 * (size_t)b->max_cells), "cudaMalloc(fields)");
+    BCK(b, cudaMalloc(&b->pops64, sizeof(double) * (size_t)b->Q * (size_t)b->max_cells), "cudaMalloc(pops64)");
+    return LEE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lee_status lee_batch_create(int32_t set, int32_t storage, const lee_batch_domain *domains, int32_t count,
+                            void *cuda_stream, lee_batch **out) {
+    if (!out) return LEE_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!domains || count < 1 || count > 65535) return LEE_ERR_INVALID_ARGUMENT;
+    if (set != LEE_D2Q5 && set != LEE_D2Q5_DIATOMIC) return LEE_ERR_UNSUPPORTED;
+    if (storage != LEE_STORE_F32 && storage != LEE_STORE_F64) return LEE_ERR_UNSUPPORTED;
+    long long total = 0, maxc = 0;
+    for (int d = 0; d < count; ++d) {
+        const lee_batch_domain &D = domains[d];
+        if (D.nx < 1 || D.ny < 1 || D.nx > (1 << 30) || D.ny > (1 << 30)) return LEE_ERR_INVALID_ARGUMENT;
+        if (!(D.tau == D.tau) || D.tau > 1e300) return LEE_ERR_INVALID_ARGUMENT;
+        if (D.tau < 0.5) return LEE_ERR_UNSTABLE_TAU;
+        const long long c = D.nx * D.ny;
+        if (c >= (1LL << 31)) return LEE_ERR_INVALID_ARGUMENT;
+        total += c;
+        maxc = std::max(maxc, c);
+    }
+    lee_batch *b = new (std::nothrow) lee_batch();
+    if (!b) return LEE_ERR_OUT_OF_MEMORY;
+    b->set = set;
+    b->storage = storage;
+    b->count = count;
+    b->ops = set_ops(set);
+    b->Q = b->ops->Q;
+    b->elem = storage == LEE_STORE_F32 ? 4 : 8;
+    b->doms.assign(domains, domains + count);
+    long long off = 0;
+    for (int d = 0; d < count; ++d) {
+        const long long c = domains[d].nx * domains[d].ny;
+        const long long p = (c + 63) / 64 * 64;
+        b->offset.push_back(off);
+        b->pitch.push_back(p);
+        b->cells.push_back(c);
+        off += p * b->Q;
+    }
+    b->total_elems = off;
+    b->total_cells = total;
+    b->max_cells = maxc;
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    b->red_blocks = aux_blocks(maxc, kReduceThreads);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->buf[0], b->elem * (size_t)off);
+    if (e == cudaSuccess) e = cudaMalloc(&b->buf[1], b->elem * (size_t)off);
+    if (e == cudaSuccess) e = cudaMalloc(&b->partial, sizeof(double) * kReduceMax * (size_t)b->red_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&b->red_out, sizeof(double) * kReduceMax);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[0], 0, b->elem * (size_t)off, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->buf[1], 0, b->elem * (size_t)off, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) {
+        lee_status s = e == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA;
+        lee_batch_destroy(b);
+        cudaGetLastError();
+        return s;
+    }
+    *out = b;
+    return LEE_OK;
+}
+
+lee_status lee_batch_init_fields(lee_batch *b, int32_t d, const double *rho, const double *u, const double *theta,
+                                 int32_t on_device) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (d < 0 || d >= b->count || !rho || !u || !theta) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "init_fields: bad args");
+    const long long c = b->cells[d];
+    const double *dr = rho, *du = u, *dt = theta;
+    if (!on_device) {
+        if ((s = ensure_aux(b)) != LEE_OK) return s;
+        const size_t n = sizeof(double) * (size_t)c;
+        BCK(b, cudaMemcpyAsync(b->fields, rho, n, cudaMemcpyHostToDevice, b->st), "H2D rho");
+        BCK(b, cudaMemcpyAsync(b->fields + c, u, 2 * n, cudaMemcpyHostToDevice, b->st), "H2D u");
+        BCK(b, cudaMemcpyAsync(b->fields + 3 * c, theta, n, cudaMemcpyHostToDevice, b->st), "H2D theta");
+        dr = b->fields;
+        du = b->fields + c;
+        dt = b->fields + 3 * c;
+    }
+    BCK(b, b->ops->init(b->storage, dr, du, dt, dom_ptr(b, b->cur, d), c, b->pitch[d], consts_for(b->set, 1.0), b->st),
+        "init kernel");
+    if (!on_device) BCK(b, cudaStreamSynchronize(b->st), "sync");
+    return LEE_OK;
+}
+
+lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (n < 0 || mode < LEE_BATCH_GRAPH || mode > LEE_BATCH_SEQUENTIAL)
+        return bfail(b, LEE_ERR_INVALID_ARGUMENT, "step: bad n or mode");
+    if (mode == LEE_BATCH_SEQUENTIAL) {
+        StepLaunch L{};
+        L.storage = b->storage;
+        L.nz = 1;
+        L.open = false;
+        L.stream = b->st;
+        for (int64_t t = 0; t < n; ++t) {
+            for (int d = 0; d < b->count; ++d) {
+                L.src = dom_ptr(b, b->cur, d);
+                L.dst = dom_ptr(b, b->cur ^ 1, d);
+                L.nx = (int)b->doms[d].nx;
+                L.ny = (int)b->doms[d].ny;
+                L.pitch = b->pitch[d];
+                L.omega = omega_for(b->storage, b->doms[d].tau);
+                fold_coefficients(b->set, false, L.omega, L.coefM, L.coefN);
+                BCK(b, b->ops->step(L), "sequential launch");
+            }
+            b->cur ^= 1;
+        }
+        return LEE_OK;
+    }
+    if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
+    int64_t left = n;
+    if (mode == LEE_BATCH_GRAPH) {
+        // up to kMaxGraphSteps steps: one graph of all of them (one launch of the whole run);
+        // longer runs: replays of a kChunkSteps graph
+        const long long glen = left <= lee_batch::kMaxGraphSteps ? (left & ~1LL) : lee_batch::kChunkSteps;
+        while (glen > 0 && left >= glen) {
+            cudaGraphExec_t ex = nullptr;
+            if ((s = ensure_graph(b, b->cur, glen, &ex)) != LEE_OK) return s;
+            BCK(b, cudaGraphLaunch(ex, b->st), "graph launch");  // even length: parity kept
+            left -= glen;
+        }
+    }
+    for (; left > 0; --left) {
+        if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
+        b->cur ^= 1;
+    }
+    return LEE_OK;
+}
+
+lee_status lee_batch_moments(lee_batch *b, int32_t d, double *rho, double *u, double *theta, int32_t on_device) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (d < 0 || d >= b->count) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "moments: bad domain");
+    const long long c = b->cells[d];
+    const SetConsts k = consts_for(b->set, 1.0);
+    if (on_device) {
+        BCK(b, b->ops->moments(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], k, rho, u, theta, b->st), "moments");
+        return LEE_OK;
+    }
+    if ((s = ensure_aux(b)) != LEE_OK) return s;
+    BCK(b, b->ops->moments(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], k, b->fields, b->fields + c,
+                           b->fields + 3 * c, b->st),
+        "moments");
+    const size_t nb = sizeof(double) * (size_t)c;
+    if (rho) BCK(b, cudaMemcpyAsync(rho, b->fields, nb, cudaMemcpyDeviceToHost, b->st), "D2H rho");
+    if (u) BCK(b, cudaMemcpyAsync(u, b->fields + c, 2 * nb, cudaMemcpyDeviceToHost, b->st), "D2H u");
+    if (theta) BCK(b, cudaMemcpyAsync(theta, b->fields + 3 * c, nb, cudaMemcpyDeviceToHost, b->st), "D2H theta");
+    BCK(b, cudaStreamSynchronize(b->st), "sync");
+    return LEE_OK;
+}
+
+lee_status lee_batch_reduce(lee_batch *b, int32_t d, double *out, int32_t on_device) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (d < 0 || d >= b->count || !out) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "reduce: bad args");
+    const long long c = b->cells[d];
+    const int nblocks = aux_blocks(c, kReduceThreads);
+    BCK(b, b->ops->reduce_partial(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], consts_for(b->set, 1.0), b->partial,
+                                  nblocks, b->st),
+        "reduce_partial");
+    double *dst = on_device ? out : b->red_out;
+    k_reduce_final<<<6, 32, 0, b->st>>>(b->partial, nblocks, 6, dst);
+    BCK(b, cudaGetLastError(), "reduce_final");
+    if (!on_device) {
+        BCK(b, cudaMemcpyAsync(out, b->red_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, b->st), "D2H reduce");
+        BCK(b, cudaStreamSynchronize(b->st), "sync");
+    }
+    return LEE_OK;
+}
+
+lee_status lee_batch_get_populations(lee_batch *b, int32_t d, double *g, int32_t on_device) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (d < 0 || d >= b->count || !g) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "get_populations: bad args");
+    const long long c = b->cells[d];
+    double *dst = g;
+    if (!on_device) {
+        if ((s = ensure_aux(b)) != LEE_OK) return s;
+        dst = b->pops64;
+    }
+    BCK(b, b->ops->export_f64(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], consts_for(b->set, 1.0), dst, b->st),
+        "export");
+    if (!on_device) {
+        BCK(b, cudaMemcpyAsync(g, dst, sizeof(double) * (size_t)b->Q * c, cudaMemcpyDeviceToHost, b->st), "D2H g");
+        BCK(b, cudaStreamSynchronize(b->st), "sync");
+    }
+    return LEE_OK;
+}
+
+lee_status lee_batch_tune(lee_batch *b, int32_t *threads, int32_t *cells_per_thread) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
+    if (threads) *threads = b->threads;
+    if (cells_per_thread) *cells_per_thread = b->V;
+    return LEE_OK;
+}
+
+lee_status lee_batch_set_tuning(lee_batch *b, int32_t threads, int32_t cells_per_thread) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    const int vf = full_vec(b->storage);
+    if ((threads != 128 && threads != 256 && threads != 512) ||
+        (cells_per_thread != vf && cells_per_thread != vf / 2))
+        return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_tuning: not a candidate shape");
+    for (const auto &d : b->doms)
+        if (d.nx % cells_per_thread) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_tuning: width does not divide nx");
+    if ((s = build_shape(b, threads, cells_per_thread)) != LEE_OK) return s;
+    b->tuned = true;
+    return LEE_OK;
+}
+
+lee_status lee_batch_cells(lee_batch *b, int64_t *cells) {
+    if (!b || !cells) return LEE_ERR_INVALID_ARGUMENT;
+    *cells = b->total_cells;
+    return LEE_OK;
+}
+
+lee_status lee_batch_sync(lee_batch *b) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    BCK(b, cudaStreamSynchronize(b->st), "sync");
+    return LEE_OK;
+}
+
+const char *lee_batch_last_error(lee_batch *b) { return b ? b->err.c_str() : "NULL batch"; }
+
+lee_status lee_batch_destroy(lee_batch *b) {
+    if (!b) return LEE_OK;
+    cudaSetDevice(b->device);
+    if (b->st) cudaStreamSynchronize(b->st);
+    drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->buf[0]);
+    cudaFree(b->buf[1]);
+    cudaFree(b->d_doms);
+    cudaFree(b->d_table);
+    cudaFree(b->fields);
+    cudaFree(b->pops64);
+    cudaFree(b->partial);
+    cudaFree(b->red_out);
+    delete b;
+    cudaGetLastError();
+    return LEE_OK;
+}
+
+}  // extern "C"

@@ -139,10 +139,17 @@ struct GridDesc {
 //     g*_i = (1 - w) g_i + sum_s M[t][s] P_s + c_i . (sum_s N[t][s] J_s),     w = 1/tau,
 // where M and N contain w, f*, the coefficients a1, a2, b, c1, c2, gamma, theta0, rho0 and the
 // energies (|c|^2 + beta)/2 (built by the host; exact algebra of Secs. 4-6).
+// Conservation of rho', j and the energy moment is an exact identity between these coefficients.
+// To keep it exact in FP32 arithmetic, every coefficient is derived from the already rounded w,
+// 1 - w is formed in the arithmetic type (exact for 1/2 <= w <= 2), and M is carried as a pair
+// M + Mlo (Mlo = the rounding residual of M, zero when M is representable); N is w times a
+// power of two for every set and needs no residual.  Rounding of the coefficients then adds no
+// systematic drift; only the (unbiased) rounding of the arithmetic remains.
 template <class C>
 struct CollideCoef {
     C one_minus_omega;
     C M[4][4];
+    C Mlo[4][4];
     C N[4][4];
 };
 
@@ -181,6 +188,12 @@ __device__ __forceinline__ void collide_cell(const C (&g)[S::Q][V], C (&out)[S::
         constexpr int t = decltype(T)::value;
         if constexpr (shell_present<S>(t)) {
             C acc = C(-0.0);
+            if constexpr (std::is_same<C, float>::value) {
+                static_for<4>([&](auto Sx) {
+                    constexpr int s = decltype(Sx)::value;
+                    if constexpr (shell_present<S>(s)) acc = fma(cf.Mlo[t][s], P[s], acc);
+                });
+            }
             static_for<4>([&](auto Sx) {
                 constexpr int s = decltype(Sx)::value;
                 if constexpr (shell_present<S>(s)) acc = fma(cf.M[t][s], P[s], acc);
@@ -232,12 +245,14 @@ __device__ __forceinline__ C sponge_factor(int x, int y, int z, const GridDesc &
 // ---------------------------------------------------------------------------------------------
 // fused pull-stream + collide, one time step
 // ---------------------------------------------------------------------------------------------
+// One thread's share of a step: V cells starting at chunk `raw` of the grid gd.  All 32 lanes of
+// the warp must call this together (warp shuffles); lanes with raw >= nchunks compute on a clamped
+// chunk and store nothing.
 template <class S, class T, int V, bool OPEN>
-__global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
-                                                        CollideCoef<typename Store<T>::C> cf,
-                                                        OpenEdge<typename Store<T>::C> ob) {
+__device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, T *__restrict__ dst, const GridDesc &gd,
+                                                     const CollideCoef<typename Store<T>::C> &cf,
+                                                     const OpenEdge<typename Store<T>::C> &ob, long long raw) {
     using C = typename Store<T>::C;
-    const long long raw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = raw < gd.nchunks;
     const long long chunk = active ? raw : gd.nchunks - 1;
     const int lane = threadIdx.x & 31;
@@ -339,6 +354,38 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
             store_vec<T, V>(outp + (long long)i * gd.pitch, post[i]);
         });
     }
+}
+
+// One fused time step on one grid: one thread per V-cell chunk.
+template <class S, class T, int V, bool OPEN>
+__global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
+                                                        CollideCoef<typename Store<T>::C> cf,
+                                                        OpenEdge<typename Store<T>::C> ob) {
+    stream_collide_chunk<S, T, V, OPEN>(src, dst, gd, cf, ob, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
+// blocks [first_block[d], first_block[d+1]); its populations start at element offset[d] of the
+// shared buffers, and it has its own extents and relaxation coefficients (its own tau).  The
+// block -> domain map is a table, so a block never straddles two domains.
+template <class C>
+struct BatchDomain {
+    GridDesc gd;
+    CollideCoef<C> cf;
+    long long offset;
+    int first_block;
+};
+
+template <class S, class T, int V>
+__global__ void __launch_bounds__(512) k_stream_collide_batched(const T *__restrict__ src, T *__restrict__ dst,
+                                                                const BatchDomain<typename Store<T>::C> *__restrict__ doms,
+                                                                const unsigned short *__restrict__ block_domain) {
+    using C = typename Store<T>::C;
+    const int d = block_domain[blockIdx.x];
+    const BatchDomain<C> &D = doms[d];
+    const long long raw = (long long)(blockIdx.x - D.first_block) * blockDim.x + threadIdx.x;
+    const OpenEdge<C> none{0, C(0), nullptr, 0};
+    stream_collide_chunk<S, T, V, false>(src + D.offset, dst + D.offset, D.gd, D.cf, none, raw);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -10,6 +10,10 @@
 #include "../../include/lee_lbm.h"
 #include "ops.cuh"
 
+// fold_coefficients evaluates host-side constants in long double; the device pass of nvcc notes
+// that long double would be double there, which does not apply to this host-only code.
+#pragma nv_diag_suppress 20208
+
 namespace lee {
 extern const SetOps kOpsD1Q3, kOpsD2Q5, kOpsD2Q5Di, kOpsD3Q7, kOpsD3Q7Di, kOpsD3Q9, kOpsD3Q13, kOpsD3Q19;
 
@@ -52,19 +56,33 @@ SetConsts consts_for(int set, double scale) {
 // with w1_s = f*_s for the scaled 16-bit storage (stored value S g / f*) and 1 otherwise,
 // w2_s = w1_s (s + beta_s) / 2, f'_t = 1 (scaled) or f*_t, alpha_t = a1 + t c1 / 2,
 // beta_t = a2 + t c2 / 2, kE = (gamma - 1) / rho0, kR = theta0 / rho0 (Secs. 4-6).
+// `omega` must already be rounded to the arithmetic type (omega_for), so that every coefficient
+// scales the same w that 1 - w is formed from.  The shell factors are evaluated in long double
+// and snapped to a power of two when they are one to within rounding (the momentum factors
+// f*_t b / rho0 are powers of two for every set of Sec. 8).
 void fold_coefficients(int set, bool scaled, double omega, double M[4][4], double N[4][4]) {
     const SetConsts k = consts_for(set, 1.0);
     for (int t = 0; t < 4; ++t)
         for (int s = 0; s < 4; ++s) M[t][s] = N[t][s] = 0.0;
-    const double kE = (k.gamma - 1.0) / k.rho0, kR = k.theta0 / k.rho0;
+    typedef long double LD;
+    const LD kE = ((LD)k.gamma - 1.0L) / (LD)k.rho0, kR = (LD)k.theta0 / (LD)k.rho0;
+    auto snap = [](LD x) -> LD {
+        if (x == 0.0L) return x;
+        int e = 0;
+        const LD m = std::frexp(std::fabs(x), &e);
+        if (std::fabs(m - 0.5L) < 1e-15L) return std::copysign(std::ldexp(0.5L, e), x);
+        return x;
+    };
     for (int t = 0; t < 4; ++t) {
-        const double ft = scaled ? 1.0 : k.f[t];
-        const double alpha = k.a1 + 0.5 * t * k.c1, beta = k.a2 + 0.5 * t * k.c2;
+        const LD ft = scaled ? 1.0L : (LD)k.f[t];
+        const LD alpha = (LD)k.a1 + 0.5L * t * (LD)k.c1, beta = (LD)k.a2 + 0.5L * t * (LD)k.c2;
         for (int s = 0; s < 4; ++s) {
-            const double w1 = scaled ? k.f[s] : 1.0;
-            const double w2 = 0.5 * (s + k.beta[s]) * w1;
-            M[t][s] = omega * ft * (alpha * w1 + beta * (kE * w2 - kR * w1));
-            N[t][s] = omega * ft * (k.b / k.rho0) * w1;
+            const LD w1 = scaled ? (LD)k.f[s] : 1.0L;
+            const LD w2 = 0.5L * ((LD)s + (LD)k.beta[s]) * w1;
+            const LD mhat = snap(ft * (alpha * w1 + beta * (kE * w2 - kR * w1)));
+            const LD nhat = snap(ft * ((LD)k.b / (LD)k.rho0) * w1);
+            M[t][s] = (double)((LD)omega * mhat);
+            N[t][s] = (double)((LD)omega * nhat);
         }
     }
 }
@@ -329,7 +347,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.nz = (int)h->cfg.nz;
     L.pitch = h->pitch;
     L.open = h->cfg.bc != LEE_BC_PERIODIC;
-    L.omega = 1.0 / h->cfg.tau;
+    L.omega = omega_for(h->cfg.storage, h->cfg.tau);
     const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
     fold_coefficients(h->cfg.set, is16, L.omega, L.coefM, L.coefN);
     L.sponge_w = h->cfg.bc == LEE_BC_OPEN_SPONGE ? h->cfg.sponge_width : 0;

@@ -18,8 +18,8 @@ struct StepLaunch {
     int nx, ny, nz;
     long long pitch;
     bool open;
-    double omega;        // 1 / tau
-    double coefM[4][4];  // see CollideCoef
+    double omega;        // 1 / tau, already rounded to the arithmetic type (see fold_coefficients)
+    double coefM[4][4];  // see CollideCoef (FP64 values, split into hi + lo for FP32 arithmetic)
     double coefN[4][4];
     int sponge_w;
     double sponge_smax;
@@ -57,6 +57,26 @@ struct SetOps {
 };
 
 const SetOps *set_ops(int set);
+
+// 1/tau rounded to the arithmetic type of the storage (FP64 storage: FP64, else FP32).
+inline double omega_for(int storage, double tau) {
+    const double w = 1.0 / tau;
+    return storage == LEE_STORE_F64 ? w : (double)(float)w;
+}
+
+// CollideCoef for arithmetic type C from FP64 coefficients (M split into hi + lo for FP32).
+template <class C>
+CollideCoef<C> make_coef(double omega, const double M[4][4], const double N[4][4]) {
+    CollideCoef<C> cf;
+    cf.one_minus_omega = (C)1 - (C)omega;
+    for (int t = 0; t < 4; ++t)
+        for (int s = 0; s < 4; ++s) {
+            cf.M[t][s] = (C)M[t][s];
+            cf.Mlo[t][s] = (C)(M[t][s] - (double)cf.M[t][s]);
+            cf.N[t][s] = (C)N[t][s];
+        }
+    return cf;
+}
 
 // Host-side velocity-set constants (the same compile-time tables the kernels use).
 template <class S>

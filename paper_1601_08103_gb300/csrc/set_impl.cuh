@@ -15,13 +15,7 @@ cudaError_t launch_step_v(const StepLaunch &L) {
     gd.nxc = L.nx / V;
     gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
     gd.pitch = L.pitch;
-    CollideCoef<C> cf;
-    cf.one_minus_omega = (C)(1.0 - L.omega);
-    for (int t = 0; t < 4; ++t)
-        for (int s = 0; s < 4; ++s) {
-            cf.M[t][s] = (C)L.coefM[t][s];
-            cf.N[t][s] = (C)L.coefN[t][s];
-        }
+    const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
     OpenEdge<C> ob;
     ob.sponge_w = L.sponge_w;
     ob.sponge_smax = (C)L.sponge_smax;
