@@ -150,8 +150,10 @@ lee_status lee_lbm_get_populations(lee_lbm *h, double *g, int32_t on_device);
  * with get_populations a resumed run equals the uninterrupted one bit for bit. */
 lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_device);
 
-/* Installs the boundary network for LEE_BC_OPEN_LEARNED (see lee_mlp.h for the parameter
- * layout).  params: nparams FP32 values, host memory. */
+/* Installs the boundary network for LEE_BC_OPEN_LEARNED on a LEE_D2Q5 grid (see lee_mlp.h for
+ * the network and its parameter layout).  params: nparams = 5313 FP32 values, host memory.  With
+ * the network installed, every step first evaluates it on the edge strips of the current state
+ * and then streams with its predictions as the entering populations. */
 lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t nparams);
 
 /* Number of time steps taken since the last init/set_populations. */

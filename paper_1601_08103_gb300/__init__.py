@@ -472,3 +472,116 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------------------------------
+# include/lee_mlp.h
+# ------------------------------------------------------------------------------------------
+MLP_NPARAM = 5313
+MLP_IN = 16
+
+_SIGS.update({
+    "lee_mlp_create": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
+    "lee_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "lee_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "lee_mlp_forward": (ctypes.c_int, [_P, _P, _I64, _P]),
+    "lee_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _I64, _P, _P]),
+    "lee_mlp_adam_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "lee_batch_edge_samples": (ctypes.c_int, [_P, _I64, _I64, _I64, _I64, _P, _P, _P]),
+    "lee_lbm_edge_inputs": (ctypes.c_int, [_P, _P, _P]),
+    "lee_mlp_destroy": (ctypes.c_int, [_P]),
+})
+
+
+def _dev(x):
+    a, on = _addr(x)
+    if x is not None and not on:
+        raise ValueError("device buffer expected")
+    return a
+
+
+def lee_mlp_create(params=None, stream=None) -> int:
+    lib = load()
+    pa = None
+    if params is not None:
+        pa, on = _addr(params)
+        if on:
+            raise ValueError("parameters are read from host memory")
+    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    h = _P()
+    _check(lib.lee_mlp_create(pa, st, ctypes.byref(h)), "lee_mlp_create")
+    return h.value
+
+
+def lee_mlp_get_params(m, out):
+    _check(_lib.lee_mlp_get_params(m, _addr(out)[0]), "lee_mlp_get_params")
+
+
+def lee_mlp_set_params(m, params):
+    _check(_lib.lee_mlp_set_params(m, _addr(params)[0]), "lee_mlp_set_params")
+
+
+def lee_mlp_forward(m, x, rows, y):
+    _check(_lib.lee_mlp_forward(m, _dev(x), int(rows), _dev(y)), "lee_mlp_forward")
+
+
+def lee_mlp_loss_grad(m, x, t, rows, grad=None, loss=None):
+    _check(_lib.lee_mlp_loss_grad(m, _dev(x), _dev(t), int(rows), _dev(grad), _dev(loss)), "lee_mlp_loss_grad")
+
+
+def lee_mlp_adam_step(m, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(_lib.lee_mlp_adam_step(m, lr, beta1, beta2, eps), "lee_mlp_adam_step")
+
+
+def lee_batch_edge_samples(b, x0, y0, nx, ny, x, t, s=None):
+    _check(_lib.lee_batch_edge_samples(b, int(x0), int(y0), int(nx), int(ny), _dev(x), _dev(t), _dev(s)),
+           "lee_batch_edge_samples", batch=b)
+
+
+def lee_lbm_edge_inputs(h, x, s=None):
+    _check(_lib.lee_lbm_edge_inputs(h, _dev(x), _dev(s)), "lee_lbm_edge_inputs", h)
+
+
+def lee_mlp_destroy(m):
+    if m:
+        _check(_lib.lee_mlp_destroy(m), "lee_mlp_destroy")
+
+
+class Mlp:
+    """Owns one lee_mlp; methods map one-to-one onto the C entry points."""
+
+    def __init__(self, params=None, stream=None):
+        load()
+        self.m = lee_mlp_create(params, stream)
+
+    def get_params(self, out):
+        lee_mlp_get_params(self.m, out)
+
+    def set_params(self, params):
+        lee_mlp_set_params(self.m, params)
+
+    def forward(self, x, rows, y):
+        lee_mlp_forward(self.m, x, rows, y)
+
+    def loss_grad(self, x, t, rows, grad=None, loss=None):
+        lee_mlp_loss_grad(self.m, x, t, rows, grad, loss)
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        lee_mlp_adam_step(self.m, lr, beta1, beta2, eps)
+
+    def close(self):
+        if self.m:
+            lee_mlp_destroy(self.m)
+            self.m = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

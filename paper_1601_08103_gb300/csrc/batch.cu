@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/lee_batch.h"
+#include "handles.cuh"
 #include "set_impl.cuh"
 
 namespace lee {
@@ -28,8 +29,6 @@ cudaError_t launch_batched(const void *src, void *dst, const void *doms, const u
         static_cast<const T *>(src), static_cast<T *>(dst), static_cast<const BatchDomain<C> *>(doms), table);
     return cudaGetLastError();
 }
-
-using BatchedFn = cudaError_t (*)(const void *, void *, const void *, const unsigned short *, int, int, cudaStream_t);
 
 template <class S, class T>
 BatchedFn batched_fn(int V) {
@@ -52,35 +51,6 @@ BatchedFn pick_batched(int set, int storage, int V) {
 
 using namespace lee;
 
-struct lee_batch {
-    int set = 0, storage = 0, count = 0, Q = 0;
-    const SetOps *ops = nullptr;
-    size_t elem = 0;
-    int device = 0;
-    std::vector<lee_batch_domain> doms;
-    std::vector<long long> offset, pitch, cells;
-    long long total_elems = 0, total_cells = 0, max_cells = 0;
-    void *buf[2] = {nullptr, nullptr};
-    int cur = 0;
-    cudaStream_t st = nullptr, cap = nullptr;
-    // launch shape
-    bool tuned = false;
-    int threads = 0, V = 0, nblocks = 0;
-    void *d_doms = nullptr;
-    unsigned short *d_table = nullptr;
-    size_t d_doms_cap = 0, d_table_cap = 0;
-    BatchedFn fn = nullptr;
-    // captured graphs, keyed by (starting parity, number of steps); every graph has an even
-    // number of steps, so replaying it leaves the buffer parity unchanged
-    static constexpr int kMaxGraphSteps = 4096;
-    static constexpr int kChunkSteps = 100;
-    std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
-    // aux
-    double *fields = nullptr, *pops64 = nullptr, *partial = nullptr, *red_out = nullptr;
-    int red_blocks = 0;
-    bool poisoned = false;
-    std::string err;
-};
 
 namespace {
 

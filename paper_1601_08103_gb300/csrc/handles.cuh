@@ -1,0 +1,76 @@
+// handles.cuh -- the opaque handle types of the C ABI, shared by the translation units that
+// implement them (lee_lbm.cu, batch.cu, mlp.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lee_batch.h"
+#include "../../include/lee_lbm.h"
+#include "ops.cuh"
+
+struct lee_lbm {
+    lee_lbm_config cfg{};
+    const lee::SetOps *ops = nullptr;
+    int device = 0;
+    int D = 0, Q = 0;
+    long long cells = 0, pitch = 0;
+    size_t elem = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *fields = nullptr;  // (D + 2) * cells FP64 staging for host fields
+    double *pops64 = nullptr;  // Q * cells FP64 staging for host populations
+    double *partial = nullptr;
+    int nblocks = 0;
+    double *red_out = nullptr;
+    unsigned int *maxbits = nullptr;
+    cudaStream_t st = nullptr;
+    long long steps = 0;
+    double scale = 1.0;
+    bool poisoned = false;
+    std::string err;
+    // learned boundary: entering populations [4][ghost_L] in the arithmetic type, and the
+    // network's packed BF16 weights (MlpDev layout, mlp.cuh)
+    void *ghost = nullptr;
+    int ghost_L = 0;
+    void *mlp = nullptr;
+    bool mlp_ready = false;
+};
+
+namespace lee {
+using BatchedFn = cudaError_t (*)(const void *, void *, const void *, const unsigned short *, int, int, cudaStream_t);
+}
+
+struct lee_batch {
+    int set = 0, storage = 0, count = 0, Q = 0;
+    const lee::SetOps *ops = nullptr;
+    size_t elem = 0;
+    int device = 0;
+    std::vector<lee_batch_domain> doms;
+    std::vector<long long> offset, pitch, cells;
+    long long total_elems = 0, total_cells = 0, max_cells = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    cudaStream_t st = nullptr, cap = nullptr;
+    // launch shape
+    bool tuned = false;
+    int threads = 0, V = 0, nblocks = 0;
+    void *d_doms = nullptr;
+    unsigned short *d_table = nullptr;
+    size_t d_doms_cap = 0, d_table_cap = 0;
+    lee::BatchedFn fn = nullptr;
+    // captured graphs, keyed by (starting parity, number of steps); every graph has an even
+    // number of steps, so replaying it leaves the buffer parity unchanged
+    static constexpr int kMaxGraphSteps = 4096;
+    static constexpr int kChunkSteps = 100;
+    std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
+    // aux
+    double *fields = nullptr, *pops64 = nullptr, *partial = nullptr, *red_out = nullptr;
+    int red_blocks = 0;
+    bool poisoned = false;
+    std::string err;
+};

@@ -8,13 +8,16 @@
 #include <string>
 
 #include "../../include/lee_lbm.h"
-#include "ops.cuh"
+#include "handles.cuh"
 
 // fold_coefficients evaluates host-side constants in long double; the device pass of nvcc notes
 // that long double would be double there, which does not apply to this host-only code.
 #pragma nv_diag_suppress 20208
 
 namespace lee {
+cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, long long pitch, int NX, int NY, void *ghost,
+                                int L, cudaStream_t st);
+cudaError_t mlp_pack(const float *params_dev, void *packed, cudaStream_t st);
 extern const SetOps kOpsD1Q3, kOpsD2Q5, kOpsD2Q5Di, kOpsD3Q7, kOpsD3Q7Di, kOpsD3Q9, kOpsD3Q13, kOpsD3Q19;
 
 const SetOps *set_ops(int set) {
@@ -91,32 +94,6 @@ void fold_coefficients(int set, bool scaled, double omega, double M[4][4], doubl
 
 using namespace lee;
 
-struct lee_lbm {
-    lee_lbm_config cfg{};
-    const SetOps *ops = nullptr;
-    int device = 0;
-    int D = 0, Q = 0;
-    long long cells = 0, pitch = 0;
-    size_t elem = 0;
-    void *buf[2] = {nullptr, nullptr};
-    int cur = 0;
-    double *fields = nullptr;  // (D + 2) * cells FP64 staging for host fields
-    double *pops64 = nullptr;  // Q * cells FP64 staging for host populations
-    double *partial = nullptr;
-    int nblocks = 0;
-    double *red_out = nullptr;
-    unsigned int *maxbits = nullptr;
-    cudaStream_t st = nullptr;
-    long long steps = 0;
-    double scale = 1.0;
-    bool poisoned = false;
-    std::string err;
-    // learned boundary
-    void *ghost = nullptr;
-    int ghost_L = 0;
-    float *mlp = nullptr;
-    long long mlp_n = 0;
-};
 
 namespace {
 
@@ -339,7 +316,8 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     lee_status s = enter(h);
     if (s != LEE_OK) return s;
     if (n < 0) return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: n < 0");
-    if (h->cfg.bc == LEE_BC_OPEN_LEARNED) return fail(h, LEE_ERR_UNSUPPORTED, "learned boundary not installed");
+    const bool learned = h->cfg.bc == LEE_BC_OPEN_LEARNED;
+    if (learned && !h->mlp_ready) return fail(h, LEE_ERR_INVALID_ARGUMENT, "learned boundary: no network installed");
     StepLaunch L{};
     L.storage = h->cfg.storage;
     L.nx = (int)h->cfg.nx;
@@ -352,13 +330,18 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     fold_coefficients(h->cfg.set, is16, L.omega, L.coefM, L.coefN);
     L.sponge_w = h->cfg.bc == LEE_BC_OPEN_SPONGE ? h->cfg.sponge_width : 0;
     L.sponge_smax = h->cfg.sponge_strength;
-    L.ghost = nullptr;
-    L.ghost_L = 0;
+    L.ghost = learned ? h->ghost : nullptr;
+    L.ghost_L = learned ? h->ghost_L : 0;
     L.force_scalar = 0;
     L.stream = h->st;
     for (int64_t t = 0; t < n; ++t) {
         L.src = h->buf[h->cur];
         L.dst = h->buf[h->cur ^ 1];
+        if (learned)
+            LEE_CK(h,
+                   launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[h->cur], h->pitch, (int)h->cfg.nx, (int)h->cfg.ny,
+                                       h->ghost, h->ghost_L, h->st),
+                   "boundary network launch");
         LEE_CK(h, h->ops->step(L), "stream_collide launch");
         h->cur ^= 1;
         h->steps++;
@@ -451,9 +434,19 @@ lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_devic
 lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t nparams) {
     lee_status s = enter(h);
     if (s != LEE_OK) return s;
-    (void)params;
-    (void)nparams;
-    return fail(h, LEE_ERR_UNSUPPORTED, "learned boundary not built yet");
+    if (h->cfg.bc != LEE_BC_OPEN_LEARNED) return fail(h, LEE_ERR_INVALID_ARGUMENT, "set_boundary_mlp: bc is not learned");
+    if (h->cfg.set != LEE_D2Q5) return fail(h, LEE_ERR_UNSUPPORTED, "set_boundary_mlp: five-velocity monoatomic set only");
+    if (!params || nparams != 5313) return fail(h, LEE_ERR_INVALID_ARGUMENT, "set_boundary_mlp: need 5313 parameters");
+    float *tmp = nullptr;
+    if (!h->mlp) LEE_CK(h, cudaMalloc(&h->mlp, 20480), "cudaMalloc(network)");
+    LEE_CK(h, cudaMalloc(&tmp, sizeof(float) * 5313), "cudaMalloc(params)");
+    cudaError_t e = cudaMemcpyAsync(tmp, params, sizeof(float) * 5313, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = mlp_pack(tmp, h->mlp, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(tmp);
+    LEE_CK(h, e, "install network");
+    h->mlp_ready = true;
+    return LEE_OK;
 }
 
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {

@@ -1,0 +1,673 @@
+// mlp.cu -- the learned boundary network (include/lee_mlp.h): packing, inference, fused
+// forward + backward on the tensor cores, deterministic gradient reduction, Adam, and the edge
+// strips of the solver state that feed it.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lee_mlp.h"
+#include "handles.cuh"
+#include "mlp.cuh"
+
+namespace lee {
+
+constexpr int kMlpWarps = 4;                 // warps per block in the network kernels
+constexpr int kChunkRows = 16 * kMlpWarps;   // rows per block and training chunk
+constexpr int kMaxTrainBlocks = 128;
+
+// ---------------------------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------------------------
+
+// FP32 parameter vector -> packed BF16 weights + FP32 biases.
+__global__ void k_mlp_pack(const float *__restrict__ p, char *__restrict__ packed) {
+    __nv_bfloat16 *w1 = reinterpret_cast<__nv_bfloat16 *>(packed + kPkW1);
+    __nv_bfloat16 *w2 = reinterpret_cast<__nv_bfloat16 *>(packed + kPkW2);
+    __nv_bfloat16 *w2t = reinterpret_cast<__nv_bfloat16 *>(packed + kPkW2T);
+    __nv_bfloat16 *w3 = reinterpret_cast<__nv_bfloat16 *>(packed + kPkW3);
+    float *b1 = reinterpret_cast<float *>(packed + kPkB1);
+    float *b2 = reinterpret_cast<float *>(packed + kPkB2);
+    float *b3 = reinterpret_cast<float *>(packed + kPkB3);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpNParam + 7 * 64; i += gridDim.x * blockDim.x) {
+        if (i >= kMlpNParam) {
+            w3[64 + (i - kMlpNParam)] = __float2bfloat16_rn(0.f);  // zero rows 1..7 of the padded W3
+            continue;
+        }
+        const float v = p[i];
+        if (i < kOffB1) {
+            w1[i - kOffW1] = __float2bfloat16_rn(v);
+        } else if (i < kOffW2) {
+            b1[i - kOffB1] = v;
+        } else if (i < kOffB2) {
+            const int r = (i - kOffW2) / kMlpHid, c = (i - kOffW2) % kMlpHid;
+            w2[r * kMlpHid + c] = __float2bfloat16_rn(v);
+            w2t[c * kMlpHid + r] = __float2bfloat16_rn(v);
+        } else if (i < kOffW3) {
+            b2[i - kOffB2] = v;
+        } else if (i < kOffB3) {
+            w3[i - kOffW3] = __float2bfloat16_rn(v);
+        } else {
+            b3[0] = v;
+        }
+    }
+}
+
+cudaError_t mlp_pack(const float *params_dev, void *packed, cudaStream_t st) {
+    k_mlp_pack<<<8, 256, 0, st>>>(params_dev, static_cast<char *>(packed));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// inference on given inputs
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpDev W, const float *__restrict__ x, long long rows,
+                                                                float *__restrict__ y) {
+    __shared__ float tile[kMlpWarps][16][kMlpIn];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long row0 = ((long long)blockIdx.x * kMlpWarps + warp) * 16;
+    for (int e = lane; e < 16 * kMlpIn; e += 32) {
+        const long long r = row0 + e / kMlpIn;
+        tile[warp][e / kMlpIn][e % kMlpIn] = r < rows ? x[r * kMlpIn + e % kMlpIn] : 0.f;
+    }
+    __syncwarp();
+    uint32_t ax[4];
+    a_frag_from_tile(tile[warp], ax);
+    MlpFwd F;
+    mlp_forward_warp(W, ax, F);
+    const int g = lane >> 2, t = lane & 3;
+    if (t == 0) {
+        if (row0 + g < rows) y[row0 + g] = F.y_lo;
+        if (row0 + g + 8 < rows) y[row0 + g + 8] = F.y_hi;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// training: fused forward + backward, per-block partial gradients
+// ---------------------------------------------------------------------------------------------
+struct TrainSmem {
+    __nv_bfloat16 xq[kChunkRows][kMlpIn];
+    __nv_bfloat16 h1q[kChunkRows][kMlpHid];
+    __nv_bfloat16 dz1q[kChunkRows][kMlpHid];
+    __nv_bfloat16 dz2q[kChunkRows][kMlpHid];
+    float xin[kMlpWarps][16][kMlpIn];
+    float db1[kMlpHid], db2[kMlpHid], dw3[kMlpHid];
+    float db3, loss;
+};
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Sum over the 8 lane groups (lanes with equal t) of a warp.
+__device__ __forceinline__ float group_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const float *__restrict__ x,
+                                                              const float *__restrict__ tgt, long long rows,
+                                                              float *__restrict__ partial, float *__restrict__ partial_loss) {
+    __shared__ TrainSmem sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) sm.db1[i] = sm.db2[i] = sm.dw3[i] = 0.f;
+    if (threadIdx.x == 0) sm.db3 = sm.loss = 0.f;
+    float accW2[8][4], accW1[2][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) accW2[j][0] = accW2[j][1] = accW2[j][2] = accW2[j][3] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) accW1[j][0] = accW1[j][1] = accW1[j][2] = accW1[j][3] = 0.f;
+    const float dscale = 2.0f / (float)rows;
+    const long long nchunks = (rows + kChunkRows - 1) / kChunkRows;
+    __syncthreads();
+
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const long long row0 = chunk * kChunkRows + warp * 16;
+        const int lr0 = warp * 16;  // first row of this warp inside the block tile
+        // ---- inputs
+        for (int e = lane; e < 16 * kMlpIn; e += 32) {
+            const long long r = row0 + e / kMlpIn;
+            const float v = r < rows ? x[r * kMlpIn + e % kMlpIn] : 0.f;
+            sm.xin[warp][e / kMlpIn][e % kMlpIn] = v;
+            sm.xq[lr0 + e / kMlpIn][e % kMlpIn] = __float2bfloat16_rn(v);
+        }
+        __syncwarp();
+        uint32_t ax[4];
+        a_frag_from_tile(sm.xin[warp], ax);
+        // ---- forward
+        MlpFwd F;
+        mlp_forward_warp(W, ax, F);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            *reinterpret_cast<uint32_t *>(&sm.h1q[lr0 + g][8 * j + 2 * t]) = F.h1[j][0];
+            *reinterpret_cast<uint32_t *>(&sm.h1q[lr0 + g + 8][8 * j + 2 * t]) = F.h1[j][1];
+        }
+        // ---- loss and dy (row g in y_lo, row g + 8 in y_hi of the t == 0 lane of the group)
+        const float ylo = __shfl_sync(0xffffffffu, F.y_lo, lane & ~3);
+        const float yhi = __shfl_sync(0xffffffffu, F.y_hi, lane & ~3);
+        const bool vlo = row0 + g < rows, vhi = row0 + g + 8 < rows;
+        const float rlo = vlo ? ylo - tgt[row0 + g] : 0.f;
+        const float rhi = vhi ? yhi - tgt[row0 + g + 8] : 0.f;
+        const float dylo = dscale * rlo, dyhi = dscale * rhi;
+        {
+            float l = (t == 0) ? rlo * rlo + rhi * rhi : 0.f;
+            l = group_sum(l);
+            if (lane == 0) atomicAdd(&sm.loss, l);
+            float d3 = (t == 0) ? dylo + dyhi : 0.f;
+            d3 = group_sum(d3);
+            if (lane == 0) atomicAdd(&sm.db3, d3);
+        }
+        // ---- layer 3 weights, dz2 = dy W3 * GELU'(z2) rounded to BF16
+        uint32_t dz2p[8][2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int col = 8 * j + 2 * t + e;
+                const float h2lo = e ? bf16_hi(F.h2[j][0]) : bf16_lo(F.h2[j][0]);
+                const float h2hi = e ? bf16_hi(F.h2[j][1]) : bf16_lo(F.h2[j][1]);
+                const float dw = group_sum(dylo * h2lo + dyhi * h2hi);
+                if (g == 0) atomicAdd(&sm.dw3[col], dw);
+            }
+            const float w3a = __bfloat162float(W.w3[8 * j + 2 * t]);
+            const float w3b = __bfloat162float(W.w3[8 * j + 2 * t + 1]);
+            dz2p[j][0] = pack_bf16(dylo * w3a * gelu_grad(F.z2[j][0]), dylo * w3b * gelu_grad(F.z2[j][1]));
+            dz2p[j][1] = pack_bf16(dyhi * w3a * gelu_grad(F.z2[j][2]), dyhi * w3b * gelu_grad(F.z2[j][3]));
+            *reinterpret_cast<uint32_t *>(&sm.dz2q[lr0 + g][8 * j + 2 * t]) = dz2p[j][0];
+            *reinterpret_cast<uint32_t *>(&sm.dz2q[lr0 + g + 8][8 * j + 2 * t]) = dz2p[j][1];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float v = e ? bf16_hi(dz2p[j][0]) + bf16_hi(dz2p[j][1]) : bf16_lo(dz2p[j][0]) + bf16_lo(dz2p[j][1]);
+                const float s = group_sum(v);
+                if (g == 0) atomicAdd(&sm.db2[8 * j + 2 * t + e], s);
+            }
+        }
+        // ---- dh1 = dz2 W2 (B[k][n] = W2[k][n] = w2t[n][k]); dz1 = dh1 * GELU'(z1) rounded to BF16
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float dh[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t a[4] = {dz2p[2 * kk][0], dz2p[2 * kk][1], dz2p[2 * kk + 1][0], dz2p[2 * kk + 1][1]};
+                const __nv_bfloat16 *w = W.w2t + (8 * j + g) * kMlpHid + 16 * kk + 2 * t;
+                mma16816(dh, a, ldw(w), ldw(w + 8));
+            }
+            const uint32_t lo = pack_bf16(dh[0] * gelu_grad(F.z1[j][0]), dh[1] * gelu_grad(F.z1[j][1]));
+            const uint32_t hi = pack_bf16(dh[2] * gelu_grad(F.z1[j][2]), dh[3] * gelu_grad(F.z1[j][3]));
+            *reinterpret_cast<uint32_t *>(&sm.dz1q[lr0 + g][8 * j + 2 * t]) = lo;
+            *reinterpret_cast<uint32_t *>(&sm.dz1q[lr0 + g + 8][8 * j + 2 * t]) = hi;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float v = e ? bf16_hi(lo) + bf16_hi(hi) : bf16_lo(lo) + bf16_lo(hi);
+                const float s = group_sum(v);
+                if (g == 0) atomicAdd(&sm.db1[8 * j + 2 * t + e], s);
+            }
+        }
+        __syncthreads();
+        // ---- weight gradients over the block's 64 rows: warp w owns output rows 16w .. 16w + 15
+        //      dW2[n][k] = sum_r dz2[r][n] h1[r][k],  dW1[n][k] = sum_r dz1[r][n] x[r][k]
+        const int m0 = 16 * warp;
+#pragma unroll
+        for (int s = 0; s < kChunkRows / 16; ++s) {
+            const int r0 = 16 * s;
+            uint32_t a2[4], a1[4];
+            a2[0] = pack2(sm.dz2q[r0 + 2 * t][m0 + g], sm.dz2q[r0 + 2 * t + 1][m0 + g]);
+            a2[1] = pack2(sm.dz2q[r0 + 2 * t][m0 + g + 8], sm.dz2q[r0 + 2 * t + 1][m0 + g + 8]);
+            a2[2] = pack2(sm.dz2q[r0 + 2 * t + 8][m0 + g], sm.dz2q[r0 + 2 * t + 9][m0 + g]);
+            a2[3] = pack2(sm.dz2q[r0 + 2 * t + 8][m0 + g + 8], sm.dz2q[r0 + 2 * t + 9][m0 + g + 8]);
+            a1[0] = pack2(sm.dz1q[r0 + 2 * t][m0 + g], sm.dz1q[r0 + 2 * t + 1][m0 + g]);
+            a1[1] = pack2(sm.dz1q[r0 + 2 * t][m0 + g + 8], sm.dz1q[r0 + 2 * t + 1][m0 + g + 8]);
+            a1[2] = pack2(sm.dz1q[r0 + 2 * t + 8][m0 + g], sm.dz1q[r0 + 2 * t + 9][m0 + g]);
+            a1[3] = pack2(sm.dz1q[r0 + 2 * t + 8][m0 + g + 8], sm.dz1q[r0 + 2 * t + 9][m0 + g + 8]);
+#pragma unroll
+            for (int jn = 0; jn < 8; ++jn) {
+                const uint32_t b0 = pack2(sm.h1q[r0 + 2 * t][8 * jn + g], sm.h1q[r0 + 2 * t + 1][8 * jn + g]);
+                const uint32_t b1 = pack2(sm.h1q[r0 + 2 * t + 8][8 * jn + g], sm.h1q[r0 + 2 * t + 9][8 * jn + g]);
+                mma16816(accW2[jn], a2, b0, b1);
+            }
+#pragma unroll
+            for (int jn = 0; jn < 2; ++jn) {
+                const uint32_t b0 = pack2(sm.xq[r0 + 2 * t][8 * jn + g], sm.xq[r0 + 2 * t + 1][8 * jn + g]);
+                const uint32_t b1 = pack2(sm.xq[r0 + 2 * t + 8][8 * jn + g], sm.xq[r0 + 2 * t + 9][8 * jn + g]);
+                mma16816(accW1[jn], a1, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- this block's partial gradient, every parameter written exactly once
+    float *out = partial + (long long)blockIdx.x * kMlpNParam;
+    const int m0 = 16 * warp;
+#pragma unroll
+    for (int jn = 0; jn < 8; ++jn) {
+        out[kOffW2 + (m0 + g) * kMlpHid + 8 * jn + 2 * t] = accW2[jn][0];
+        out[kOffW2 + (m0 + g) * kMlpHid + 8 * jn + 2 * t + 1] = accW2[jn][1];
+        out[kOffW2 + (m0 + g + 8) * kMlpHid + 8 * jn + 2 * t] = accW2[jn][2];
+        out[kOffW2 + (m0 + g + 8) * kMlpHid + 8 * jn + 2 * t + 1] = accW2[jn][3];
+    }
+#pragma unroll
+    for (int jn = 0; jn < 2; ++jn) {
+        out[kOffW1 + (m0 + g) * kMlpIn + 8 * jn + 2 * t] = accW1[jn][0];
+        out[kOffW1 + (m0 + g) * kMlpIn + 8 * jn + 2 * t + 1] = accW1[jn][1];
+        out[kOffW1 + (m0 + g + 8) * kMlpIn + 8 * jn + 2 * t] = accW1[jn][2];
+        out[kOffW1 + (m0 + g + 8) * kMlpIn + 8 * jn + 2 * t + 1] = accW1[jn][3];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
+        out[kOffB1 + i] = sm.db1[i];
+        out[kOffB2 + i] = sm.db2[i];
+        out[kOffW3 + i] = sm.dw3[i];
+    }
+    if (threadIdx.x == 0) {
+        out[kOffB3] = sm.db3;
+        partial_loss[blockIdx.x] = sm.loss;
+    }
+}
+
+// grad[i] = sum over blocks of partial[b][i], in block order; loss = sum / rows.
+__global__ void k_mlp_grad_reduce(const float *__restrict__ partial, const float *__restrict__ partial_loss, int nblocks,
+                                  long long rows, float *__restrict__ grad, float *__restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMlpNParam) {
+        float a = 0.f;
+        for (int b = 0; b < nblocks; ++b) a += partial[(long long)b * kMlpNParam + i];
+        grad[i] = a;
+    }
+    if (i == 0 && loss) {
+        float l = 0.f;
+        for (int b = 0; b < nblocks; ++b) l += partial_loss[b];
+        *loss = l / (float)rows;
+    }
+}
+
+// Adam (bias-corrected) on the FP32 master parameters.
+__global__ void k_mlp_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                           const float *__restrict__ grad, float lr, float beta1, float beta2, float eps, float corr1,
+                           float corr2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpNParam) return;
+    const float gr = grad[i];
+    const float mi = beta1 * m[i] + (1.f - beta1) * gr;
+    const float vi = beta2 * v[i] + (1.f - beta2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * corr1) / (sqrtf(vi * corr2) + eps);
+}
+
+// ---------------------------------------------------------------------------------------------
+// edge strips of D2Q5 population fields (library order 0 rest, 1 +x, 2 -x, 3 +y, 4 -y)
+// ---------------------------------------------------------------------------------------------
+__constant__ int c_canon[4][5] = {{0, 1, 2, 3, 4}, {0, 2, 1, 4, 3}, {0, 3, 4, 2, 1}, {0, 4, 3, 1, 2}};
+__constant__ int c_normal[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+
+struct EdgeRow {
+    int e, k, cx, cy;
+};
+
+// Row r of the region's border rows -> edge, position along it, and cell.
+__device__ __forceinline__ EdgeRow edge_row(int r, int x0, int y0, int nx, int ny) {
+    EdgeRow E;
+    if (r < ny) { E.e = 0; E.k = r; E.cx = x0; E.cy = y0 + r; }
+    else if (r < 2 * ny) { E.e = 1; E.k = r - ny; E.cx = x0 + nx - 1; E.cy = y0 + E.k; }
+    else if (r < 2 * ny + nx) { E.e = 2; E.k = r - 2 * ny; E.cx = x0 + E.k; E.cy = y0; }
+    else { E.e = 3; E.k = r - 2 * ny - nx; E.cx = x0 + E.k; E.cy = y0 + ny - 1; }
+    return E;
+}
+
+// 1 / f* of D2Q5 (f* = 1/2 rest, 1/8 moving), exact.
+__device__ __forceinline__ float inv_f(int i) { return i == 0 ? 2.f : 8.f; }
+
+// Strip inputs x[16] and scale s of one border row.
+template <class T>
+__device__ __forceinline__ void strip_inputs(const T *__restrict__ g, long long pitch, int NX, const EdgeRow &E, bool scaled,
+                                             float (&xv)[kMlpIn], float &s) {
+    float ss = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int px = E.cx + d * c_normal[E.e][0], py = E.cy + d * c_normal[E.e][1];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int i = c_canon[E.e][j];
+            float h = (float)Store<T>::load(g[(long long)i * pitch + px + (long long)NX * py]);
+            if (!scaled) h *= inv_f(i);
+            xv[5 * d + j] = h;
+            ss += h * h;
+        }
+    }
+    s = fmaxf(sqrtf(ss / 15.f), 1e-30f);
+    const float inv = 1.f / s;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) xv[k] *= inv;
+    xv[15] = 0.f;
+}
+
+// Training pairs from a batch: one thread per border row of one domain.
+template <class T>
+__global__ void k_edge_samples(const T *__restrict__ buf, const long long *__restrict__ offset,
+                               const long long *__restrict__ pitch, const int *__restrict__ dnx, int ndom, int x0, int y0,
+                               int nx, int ny, float *__restrict__ xo, float *__restrict__ to, float *__restrict__ so) {
+    const int R = 2 * (nx + ny);
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)ndom * R) return;
+    const int d = (int)(row / R), r = (int)(row % R);
+    const T *g = buf + offset[d];
+    const EdgeRow E = edge_row(r, x0, y0, nx, ny);
+    float xv[kMlpIn], s;
+    strip_inputs<T>(g, pitch[d], dnx[d], E, Store<T>::scaled, xv, s);
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k) xo[row * kMlpIn + k] = xv[k];
+    const int iin = c_canon[E.e][1];
+    const int ox = E.cx - c_normal[E.e][0], oy = E.cy - c_normal[E.e][1];
+    float tv = (float)Store<T>::load(g[(long long)iin * pitch[d] + ox + (long long)dnx[d] * oy]);
+    if (!Store<T>::scaled) tv *= inv_f(iin);
+    to[row] = tv / s;
+    if (so) so[row] = s;
+}
+
+// Inputs of the border of a single whole grid (no targets).
+template <class T>
+__global__ void k_edge_inputs(const T *__restrict__ g, long long pitch, int NX, int NY, float *__restrict__ xo,
+                              float *__restrict__ so) {
+    const int R = 2 * (NX + NY);
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= R) return;
+    const EdgeRow E = edge_row(row, 0, 0, NX, NY);
+    float xv[kMlpIn], s;
+    strip_inputs<T>(g, pitch, NX, E, Store<T>::scaled, xv, s);
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k) xo[(long long)row * kMlpIn + k] = xv[k];
+    if (so) so[row] = s;
+}
+
+// The learned boundary of one step: strips of the current post-collision state -> network ->
+// entering populations ghost[4][L] (arithmetic type C of the storage).
+template <class T>
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const T *__restrict__ g, long long pitch, int NX,
+                                                                 int NY, typename Store<T>::C *__restrict__ ghost, int L) {
+    using C = typename Store<T>::C;
+    __shared__ float tile[kMlpWarps][16][kMlpIn];
+    __shared__ float sc[kMlpWarps][16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = 2 * (NX + NY);
+    const int row0 = (blockIdx.x * kMlpWarps + warp) * 16;
+    if (lane < 16) {
+        const int r = row0 + lane;
+        float xv[kMlpIn], s = 1.f;
+        if (r < R) {
+            strip_inputs<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, xv, s);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kMlpIn; ++k) xv[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) tile[warp][lane][k] = xv[k];
+        sc[warp][lane] = s;
+    }
+    __syncwarp();
+    uint32_t ax[4];
+    a_frag_from_tile(tile[warp], ax);
+    MlpFwd F;
+    mlp_forward_warp(W, ax, F);
+    const int gq = lane >> 2, t = lane & 3;
+    if (t == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lr = gq + 8 * h;
+            const int r = row0 + lr;
+            if (r < R) {
+                const EdgeRow E = edge_row(r, 0, 0, NX, NY);
+                const int iin = c_canon[E.e][1];
+                float v = sc[warp][lr] * (h ? F.y_hi : F.y_lo);
+                if (!Store<T>::scaled) v /= inv_f(iin);
+                ghost[E.e * L + E.k] = (C)v;
+            }
+        }
+    }
+}
+
+template <class Fn>
+cudaError_t with_store(int storage, Fn &&fn) {
+    switch (storage) {
+    case LEE_STORE_F64: return fn((double *)nullptr);
+    case LEE_STORE_F32: return fn((float *)nullptr);
+    case LEE_STORE_F16: return fn((__half *)nullptr);
+    case LEE_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Called by lee_lbm_step for LEE_BC_OPEN_LEARNED.
+cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, long long pitch, int NX, int NY, void *ghost,
+                                int L, cudaStream_t st) {
+    const MlpDev W = mlp_dev(packed);
+    const int R = 2 * (NX + NY);
+    const int blocks = (R + kChunkRows - 1) / kChunkRows;
+    return with_store(storage, [&](auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        using C = typename Store<T>::C;
+        k_mlp_boundary<T><<<blocks, 32 * kMlpWarps, 0, st>>>(W, static_cast<const T *>(g), pitch, NX, NY,
+                                                             static_cast<C *>(ghost), L);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace lee
+
+using namespace lee;
+
+struct lee_mlp {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    void *packed = nullptr;
+    float *partial = nullptr, *partial_loss = nullptr;
+    long long adam_t = 0;
+    bool poisoned = false;
+    std::string err;
+};
+
+namespace {
+
+#define MCK(mm, call)                                                      \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) {                                           \
+            (mm)->poisoned = true;                                         \
+            (mm)->err = cudaGetErrorString(e_);                            \
+            return e_ == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA; \
+        }                                                                  \
+    } while (0)
+
+lee_status menter(lee_mlp *m) {
+    if (!m) return LEE_ERR_INVALID_ARGUMENT;
+    if (m->poisoned) return LEE_ERR_POISONED;
+    if (cudaSetDevice(m->device) != cudaSuccess) return LEE_ERR_CUDA;
+    return LEE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lee_status lee_mlp_create(const float *params, void *cuda_stream, lee_mlp **out) {
+    if (!out) return LEE_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    lee_mlp *m = new (std::nothrow) lee_mlp();
+    if (!m) return LEE_ERR_OUT_OF_MEMORY;
+    m->st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t pb = sizeof(float) * kMlpNParam;
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaMalloc(&m->p, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->m, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->v, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grad, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->packed, kMlpPackedBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&m->partial, pb * kMaxTrainBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&m->partial_loss, sizeof(float) * kMaxTrainBlocks);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, pb, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->v, 0, pb, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->grad, 0, pb, m->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->packed, 0, kMlpPackedBytes, m->st);
+    if (e == cudaSuccess) {
+        if (params)
+            e = cudaMemcpyAsync(m->p, params, pb, cudaMemcpyHostToDevice, m->st);
+        else
+            e = cudaMemsetAsync(m->p, 0, pb, m->st);
+    }
+    if (e == cudaSuccess) e = mlp_pack(m->p, m->packed, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    if (e != cudaSuccess) {
+        lee_mlp_destroy(m);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA;
+    }
+    *out = m;
+    return LEE_OK;
+}
+
+lee_status lee_mlp_get_params(lee_mlp *m, float *params) {
+    lee_status s = menter(m);
+    if (s != LEE_OK) return s;
+    if (!params) return LEE_ERR_INVALID_ARGUMENT;
+    MCK(m, cudaMemcpyAsync(params, m->p, sizeof(float) * kMlpNParam, cudaMemcpyDeviceToHost, m->st));
+    MCK(m, cudaStreamSynchronize(m->st));
+    return LEE_OK;
+}
+
+lee_status lee_mlp_set_params(lee_mlp *m, const float *params) {
+    lee_status s = menter(m);
+    if (s != LEE_OK) return s;
+    if (!params) return LEE_ERR_INVALID_ARGUMENT;
+    MCK(m, cudaMemcpyAsync(m->p, params, sizeof(float) * kMlpNParam, cudaMemcpyHostToDevice, m->st));
+    MCK(m, mlp_pack(m->p, m->packed, m->st));
+    MCK(m, cudaStreamSynchronize(m->st));
+    return LEE_OK;
+}
+
+lee_status lee_mlp_forward(lee_mlp *m, const float *x, int64_t rows, float *y) {
+    lee_status s = menter(m);
+    if (s != LEE_OK) return s;
+    if (!x || !y || rows < 0) return LEE_ERR_INVALID_ARGUMENT;
+    if (rows == 0) return LEE_OK;
+    const long long blocks = (rows + kChunkRows - 1) / kChunkRows;
+    k_mlp_forward<<<(unsigned)blocks, 32 * kMlpWarps, 0, m->st>>>(mlp_dev(m->packed), x, rows, y);
+    MCK(m, cudaGetLastError());
+    return LEE_OK;
+}
+
+lee_status lee_mlp_loss_grad(lee_mlp *m, const float *x, const float *t, int64_t rows, float *grad, float *loss) {
+    lee_status s = menter(m);
+    if (s != LEE_OK) return s;
+    if (!x || !t || rows < 1) return LEE_ERR_INVALID_ARGUMENT;
+    const long long nchunks = (rows + kChunkRows - 1) / kChunkRows;
+    const int blocks = (int)(nchunks < kMaxTrainBlocks ? nchunks : kMaxTrainBlocks);
+    k_mlp_train<<<blocks, 32 * kMlpWarps, 0, m->st>>>(mlp_dev(m->packed), x, t, rows, m->partial, m->partial_loss);
+    MCK(m, cudaGetLastError());
+    k_mlp_grad_reduce<<<(kMlpNParam + 255) / 256, 256, 0, m->st>>>(m->partial, m->partial_loss, blocks, rows, m->grad, loss);
+    MCK(m, cudaGetLastError());
+    if (grad) MCK(m, cudaMemcpyAsync(grad, m->grad, sizeof(float) * kMlpNParam, cudaMemcpyDeviceToDevice, m->st));
+    return LEE_OK;
+}
+
+lee_status lee_mlp_adam_step(lee_mlp *m, float lr, float beta1, float beta2, float eps) {
+    lee_status s = menter(m);
+    if (s != LEE_OK) return s;
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return LEE_ERR_INVALID_ARGUMENT;
+    m->adam_t++;
+    const float corr1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)m->adam_t)));
+    const float corr2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)m->adam_t)));
+    k_mlp_adam<<<(kMlpNParam + 255) / 256, 256, 0, m->st>>>(m->p, m->m, m->v, m->grad, lr, beta1, beta2, eps, corr1, corr2);
+    MCK(m, cudaGetLastError());
+    MCK(m, mlp_pack(m->p, m->packed, m->st));
+    return LEE_OK;
+}
+
+lee_status lee_batch_edge_samples(lee_batch *b, int64_t x0, int64_t y0, int64_t nx, int64_t ny, float *x, float *t,
+                                  float *s) {
+    if (!b || !x || !t) return LEE_ERR_INVALID_ARGUMENT;
+    if (b->poisoned) return LEE_ERR_POISONED;
+    if (b->set != LEE_D2Q5) return LEE_ERR_UNSUPPORTED;
+    if (nx < 3 || ny < 3 || x0 < 1 || y0 < 1) return LEE_ERR_INVALID_ARGUMENT;
+    for (const auto &d : b->doms)
+        if (x0 + nx + 1 > d.nx || y0 + ny + 1 > d.ny) return LEE_ERR_INVALID_ARGUMENT;
+    cudaSetDevice(b->device);
+    std::vector<long long> off(b->count), pit(b->count);
+    std::vector<int> dnx(b->count);
+    for (int d = 0; d < b->count; ++d) {
+        off[d] = b->offset[d];
+        pit[d] = b->pitch[d];
+        dnx[d] = (int)b->doms[d].nx;
+    }
+    long long *doff = nullptr, *dpit = nullptr;
+    int *ddnx = nullptr;
+    cudaError_t e = cudaMallocAsync(&doff, sizeof(long long) * b->count, b->st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dpit, sizeof(long long) * b->count, b->st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ddnx, sizeof(int) * b->count, b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), sizeof(long long) * b->count, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dpit, pit.data(), sizeof(long long) * b->count, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ddnx, dnx.data(), sizeof(int) * b->count, cudaMemcpyHostToDevice, b->st);
+    const long long rows = (long long)b->count * 2 * (nx + ny);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((rows + 255) / 256);
+        e = with_store(b->storage, [&](auto *tp) {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            k_edge_samples<T><<<blocks, 256, 0, b->st>>>(static_cast<const T *>(b->buf[b->cur]), doff, dpit, ddnx, b->count,
+                                                         (int)x0, (int)y0, (int)nx, (int)ny, x, t, s);
+            return cudaGetLastError();
+        });
+    }
+    cudaFreeAsync(doff, b->st);
+    cudaFreeAsync(dpit, b->st);
+    cudaFreeAsync(ddnx, b->st);
+    if (e != cudaSuccess) {
+        b->poisoned = true;
+        b->err = std::string("edge samples: ") + cudaGetErrorString(e);
+        return LEE_ERR_CUDA;
+    }
+    return LEE_OK;
+}
+
+lee_status lee_lbm_edge_inputs(lee_lbm *h, float *x, float *s) {
+    if (!h || !x) return LEE_ERR_INVALID_ARGUMENT;
+    if (h->poisoned) return LEE_ERR_POISONED;
+    if (h->cfg.set != LEE_D2Q5) return LEE_ERR_UNSUPPORTED;
+    if (h->cfg.nx < 3 || h->cfg.ny < 3) return LEE_ERR_INVALID_ARGUMENT;
+    cudaSetDevice(h->device);
+    const int NX = (int)h->cfg.nx, NY = (int)h->cfg.ny;
+    const int R = 2 * (NX + NY);
+    cudaError_t e = with_store(h->cfg.storage, [&](auto *tp) {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        k_edge_inputs<T><<<(R + 255) / 256, 256, 0, h->st>>>(static_cast<const T *>(h->buf[h->cur]), h->pitch, NX, NY, x, s);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) {
+        h->poisoned = true;
+        h->err = std::string("edge inputs: ") + cudaGetErrorString(e);
+        return LEE_ERR_CUDA;
+    }
+    return LEE_OK;
+}
+
+lee_status lee_mlp_destroy(lee_mlp *m) {
+    if (!m) return LEE_OK;
+    cudaSetDevice(m->device);
+    if (m->st) cudaStreamSynchronize(m->st);
+    cudaFree(m->p);
+    cudaFree(m->m);
+    cudaFree(m->v);
+    cudaFree(m->grad);
+    cudaFree(m->packed);
+    cudaFree(m->partial);
+    cudaFree(m->partial_loss);
+    delete m;
+    cudaGetLastError();
+    return LEE_OK;
+}
+
+}  // extern "C"
