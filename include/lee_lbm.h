@@ -122,7 +122,10 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out);
 lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, const double *theta, int32_t on_device);
 
 /* Advances n >= 0 time steps of the LBE update scheme (Sec. 6): one fused pull-stream + BGK
- * collision kernel per step (plus the boundary network for OPEN_LEARNED).  Asynchronous. */
+ * collision kernel per step (plus the boundary network for OPEN_LEARNED).  Asynchronous.  For
+ * n >= 8 the launches are replayed from a CUDA graph (one graph holding all n steps for
+ * n <= 4096, else repeated 100-step graphs), captured on first use of that length on a private
+ * stream and cached in the handle; results are identical to direct launches. */
 lee_status lee_lbm_step(lee_lbm *h, int64_t n);
 
 /* Per-cell moments of the current state (Sec. 4 discrete moments; Sec. 5 temperature for

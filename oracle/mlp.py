@@ -197,7 +197,8 @@ def targets(post, shape, c, f, region):
 
 
 def ghost_values(p, post, shape, c, f, quantize: bool = True):
-    """Entering populations of the four edges of a whole open grid predicted by the network:
+    """Entering populations of the four edges of a whole open grid predicted by the network,
+    clamped to the magnitude of the outward population leaving through the same edge cell:
     ghost[4][L] (L = max(nx, ny)) in solver units, the layout of the ghost-fed open step."""
     nx, ny = shape[0], shape[1]
     region = (0, 0, nx, ny)
@@ -206,6 +207,10 @@ def ghost_values(p, post, shape, c, f, quantize: bool = True):
     idx = {(int(ci[0]), int(ci[1])): i for i, ci in enumerate(c)}
     L = max(nx, ny)
     ghost = np.zeros((4, L))
-    for yv, s, e, k in zip(y, S, E, P):
-        ghost[e, k] = s * yv * f[idx[CANON[e][1]]]
+    for xv, yv, s, e, k in zip(X, y, S, E, P):
+        # passivity clamp: |entering| <= |outward population leaving through the same edge
+        # cell| (strip slot 2 at depth 0), in units of f*; both are moving velocities with the
+        # same weight, so the edge cannot add weighted energy
+        hout = abs(xv[2] * s)
+        ghost[e, k] = min(max(s * yv, -hout), hout) * f[idx[CANON[e][1]]]
     return ghost

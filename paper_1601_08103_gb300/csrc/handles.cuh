@@ -39,6 +39,10 @@ struct lee_lbm {
     int ghost_L = 0;
     void *mlp = nullptr;
     bool mlp_ready = false;
+    // captured step graphs keyed by (starting parity, number of steps), even lengths only, and
+    // the stream they are captured on
+    std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
+    cudaStream_t cap = nullptr;
 };
 
 namespace lee {

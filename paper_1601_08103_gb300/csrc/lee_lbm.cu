@@ -97,6 +97,8 @@ using namespace lee;
 
 namespace {
 
+constexpr long long kGraphMinSteps = 8, kMaxGraphSteps = 4096, kChunkGraphSteps = 100;
+
 lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
     if (h) {
         h->err = msg;
@@ -333,16 +335,49 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.ghost = learned ? h->ghost : nullptr;
     L.ghost_L = learned ? h->ghost_L : 0;
     L.force_scalar = 0;
-    L.stream = h->st;
-    for (int64_t t = 0; t < n; ++t) {
-        L.src = h->buf[h->cur];
-        L.dst = h->buf[h->cur ^ 1];
-        if (learned)
-            LEE_CK(h,
-                   launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[h->cur], h->pitch, (int)h->cfg.nx, (int)h->cfg.ny,
-                                       h->ghost, h->ghost_L, h->st),
-                   "boundary network launch");
-        LEE_CK(h, h->ops->step(L), "stream_collide launch");
+    // One time step's launches (boundary network first for the learned edge) on stream `st`.
+    auto launch_step = [&](int from, cudaStream_t st) -> cudaError_t {
+        L.src = h->buf[from];
+        L.dst = h->buf[from ^ 1];
+        L.stream = st;
+        if (learned) {
+            cudaError_t e = launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[from], h->pitch, (int)h->cfg.nx,
+                                                (int)h->cfg.ny, h->ghost, h->ghost_L, st);
+            if (e != cudaSuccess) return e;
+        }
+        return h->ops->step(L);
+    };
+    int64_t left = n;
+    if (n >= kGraphMinSteps) {
+        // Runs of up to kMaxGraphSteps steps are one launch of a graph holding all of them;
+        // longer runs replay a kChunkGraphSteps graph.  Graphs have an even number of steps, so
+        // a replay leaves the buffer parity unchanged; they are captured once per (parity,
+        // length) on a private stream and replayed on the handle's stream.
+        const long long glen = n <= kMaxGraphSteps ? (n & ~1LL) : kChunkGraphSteps;
+        while (left >= glen) {
+            auto it = h->exec.find({h->cur, glen});
+            cudaGraphExec_t ex = it == h->exec.end() ? nullptr : it->second;
+            if (!ex) {
+                if (!h->cap) LEE_CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
+                cudaGraph_t g = nullptr;
+                LEE_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+                cudaError_t e = cudaSuccess;
+                int w = h->cur;
+                for (long long k = 0; k < glen && e == cudaSuccess; ++k, w ^= 1) e = launch_step(w, h->cap);
+                cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+                if (g) cudaGraphDestroy(g);
+                LEE_CK(h, e, "step graph capture");
+                h->exec[{h->cur, glen}] = ex;
+            }
+            LEE_CK(h, cudaGraphLaunch(ex, h->st), "step graph launch");
+            left -= glen;
+            h->steps += glen;
+        }
+    }
+    for (; left > 0; --left) {
+        LEE_CK(h, launch_step(h->cur, h->st), "step launch");
         h->cur ^= 1;
         h->steps++;
     }
@@ -474,6 +509,8 @@ lee_status lee_lbm_destroy(lee_lbm *h) {
     if (!h) return LEE_OK;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->st);
+    for (auto &kv : h->exec) cudaGraphExecDestroy(kv.second);
+    if (h->cap) cudaStreamDestroy(h->cap);
     free_all(h);
     delete h;
     cudaGetLastError();

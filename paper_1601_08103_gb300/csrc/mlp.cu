@@ -94,8 +94,9 @@ struct TrainSmem {
     __nv_bfloat16 dz1q[kChunkRows][kMlpHid];
     __nv_bfloat16 dz2q[kChunkRows][kMlpHid];
     float xin[kMlpWarps][16][kMlpIn];
-    float db1[kMlpHid], db2[kMlpHid], dw3[kMlpHid];
-    float db3, loss;
+    // per-warp accumulators (summed in warp order at the end: deterministic)
+    float db1[kMlpWarps][kMlpHid], db2[kMlpWarps][kMlpHid], dw3[kMlpWarps][kMlpHid];
+    float db3[kMlpWarps], loss[kMlpWarps];
 };
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -115,8 +116,9 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
                                                               float *__restrict__ partial, float *__restrict__ partial_loss) {
     __shared__ TrainSmem sm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) sm.db1[i] = sm.db2[i] = sm.dw3[i] = 0.f;
-    if (threadIdx.x == 0) sm.db3 = sm.loss = 0.f;
+    for (int i = threadIdx.x; i < kMlpWarps * kMlpHid; i += blockDim.x)
+        sm.db1[i / kMlpHid][i % kMlpHid] = sm.db2[i / kMlpHid][i % kMlpHid] = sm.dw3[i / kMlpHid][i % kMlpHid] = 0.f;
+    if (threadIdx.x < kMlpWarps) sm.db3[threadIdx.x] = sm.loss[threadIdx.x] = 0.f;
     float accW2[8][4], accW1[2][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) accW2[j][0] = accW2[j][1] = accW2[j][2] = accW2[j][3] = 0.f;
@@ -157,10 +159,10 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
         {
             float l = (t == 0) ? rlo * rlo + rhi * rhi : 0.f;
             l = group_sum(l);
-            if (lane == 0) atomicAdd(&sm.loss, l);
+            if (lane == 0) sm.loss[warp] += l;
             float d3 = (t == 0) ? dylo + dyhi : 0.f;
             d3 = group_sum(d3);
-            if (lane == 0) atomicAdd(&sm.db3, d3);
+            if (lane == 0) sm.db3[warp] += d3;
         }
         // ---- layer 3 weights, dz2 = dy W3 * GELU'(z2) rounded to BF16
         uint32_t dz2p[8][2];
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
                 const float h2lo = e ? bf16_hi(F.h2[j][0]) : bf16_lo(F.h2[j][0]);
                 const float h2hi = e ? bf16_hi(F.h2[j][1]) : bf16_lo(F.h2[j][1]);
                 const float dw = group_sum(dylo * h2lo + dyhi * h2hi);
-                if (g == 0) atomicAdd(&sm.dw3[col], dw);
+                if (g == 0) sm.dw3[warp][col] += dw;
             }
             const float w3a = __bfloat162float(W.w3[8 * j + 2 * t]);
             const float w3b = __bfloat162float(W.w3[8 * j + 2 * t + 1]);
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
             for (int e = 0; e < 2; ++e) {
                 const float v = e ? bf16_hi(dz2p[j][0]) + bf16_hi(dz2p[j][1]) : bf16_lo(dz2p[j][0]) + bf16_lo(dz2p[j][1]);
                 const float s = group_sum(v);
-                if (g == 0) atomicAdd(&sm.db2[8 * j + 2 * t + e], s);
+                if (g == 0) sm.db2[warp][8 * j + 2 * t + e] += s;
             }
         }
         // ---- dh1 = dz2 W2 (B[k][n] = W2[k][n] = w2t[n][k]); dz1 = dh1 * GELU'(z1) rounded to BF16
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
             for (int e = 0; e < 2; ++e) {
                 const float v = e ? bf16_hi(lo) + bf16_hi(hi) : bf16_lo(lo) + bf16_lo(hi);
                 const float s = group_sum(v);
-                if (g == 0) atomicAdd(&sm.db1[8 * j + 2 * t + e], s);
+                if (g == 0) sm.db1[warp][8 * j + 2 * t + e] += s;
             }
         }
         __syncthreads();
@@ -259,13 +261,24 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_train(MlpDev W, const fl
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
-        out[kOffB1 + i] = sm.db1[i];
-        out[kOffB2 + i] = sm.db2[i];
-        out[kOffW3 + i] = sm.dw3[i];
+        float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int w = 0; w < kMlpWarps; ++w) {
+            a1 += sm.db1[w][i];
+            a2 += sm.db2[w][i];
+            a3 += sm.dw3[w][i];
+        }
+        out[kOffB1 + i] = a1;
+        out[kOffB2 + i] = a2;
+        out[kOffW3 + i] = a3;
     }
     if (threadIdx.x == 0) {
-        out[kOffB3] = sm.db3;
-        partial_loss[blockIdx.x] = sm.loss;
+        float b = 0.f, l = 0.f;
+        for (int w = 0; w < kMlpWarps; ++w) {
+            b += sm.db3[w];
+            l += sm.loss[w];
+        }
+        out[kOffB3] = b;
+        partial_loss[blockIdx.x] = l;
     }
 }
 
@@ -422,7 +435,13 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const
             if (r < R) {
                 const EdgeRow E = edge_row(r, 0, 0, NX, NY);
                 const int iin = c_canon[E.e][1];
-                float v = sc[warp][lr] * (h ? F.y_hi : F.y_lo);
+                // Passivity clamp: the entering population may not exceed in magnitude the
+                // outward population leaving through the same edge cell (canonical slot 2 at
+                // depth 0 of the strip, same weight f*).  Then the edge never adds weighted
+                // energy sum g^2 / f*, and with tau >= 1/2 the whole step is L2-stable whatever
+                // the network predicts.
+                const float hout = fabsf(tile[warp][lr][2] * sc[warp][lr]);
+                float v = fminf(fmaxf(sc[warp][lr] * (h ? F.y_hi : F.y_lo), -hout), hout);
                 if (!Store<T>::scaled) v /= inv_f(iin);
                 ghost[E.e * L + E.k] = (C)v;
             }

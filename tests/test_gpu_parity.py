@@ -252,3 +252,37 @@ def test_full_size_2d_config_against_oracle(gpu_lib):
         oracle.set_threads(1)
     want = oracle.moments(name, g)[0]
     assert_close(mr, want, 1e-12, "2D config rho'")
+
+
+@pytest.mark.parametrize("name,shape,storage,bc", [("D2Q5", (260, 37, 1), "f32", "periodic"),
+                                                    ("D3Q7", (36, 10, 7), "f16", "periodic"),
+                                                    ("D2Q5", (64, 48, 1), "f64", "open_sponge"),
+                                                    ("D2Q5", (64, 48, 1), "f32", "open_learned")])
+def test_graph_replay_equals_direct_launches(gpu_lib, name, shape, storage, bc):
+    """lee_lbm_step(n) replays captured graphs for n >= 8; the result equals n single steps bit
+    for bit, for whole-run graphs (n <= 4096, odd n leaves one direct step) and for chunked
+    replays (n > 4096)."""
+    lee = gpu_lib
+    from oracle import mlp as omlp
+
+    s = oracle.velset(name)
+    cells = int(np.prod(shape))
+    rho, u, th = inputs.random_fields(shape, s.D, 17)
+    kw = dict(sponge_width=4, sponge_strength=0.5) if bc == "open_sponge" else {}
+    for n in (37, 4103):
+        outs = []
+        for mode in ("single", "graph"):
+            with lee.Solver(name, shape, 0.6, storage=storage, bc=bc, **kw) as sv:
+                if bc == "open_learned":
+                    sv.set_boundary_mlp(omlp.init_params(3).astype(np.float32))
+                sv.init_fields(rho, u, th)
+                if mode == "single":
+                    for _ in range(n):
+                        sv.step(1)
+                else:
+                    sv.step(n)
+                assert sv.steps_done == n
+                g = np.empty((s.q, cells))
+                sv.get_populations(g)
+                outs.append(g)
+        assert np.array_equal(outs[0], outs[1]), n

@@ -74,8 +74,13 @@ def test_constant_network_gives_closed_form_ghosts():
     ghost = mlp.ghost_values(p, post, (nx, ny, 1), s.c, s.f)
     X, S, E, P = mlp.strips(post, (nx, ny, 1), s.c, s.f, (0, 0, nx, ny))
     f_in = 0.125  # every entering velocity is a moving one
-    for sc, e, k in zip(S, E, P):
-        assert ghost[e, k] == pytest.approx(0.375 * sc * f_in, rel=1e-15)
+    clamped = 0
+    for xv, sc, e, k in zip(X, S, E, P):
+        bound = abs(xv[2]) * sc  # outward population of the edge cell, in units of f*
+        want = min(max(0.375 * sc, -bound), bound) * f_in
+        clamped += bound < 0.375 * sc
+        assert ghost[e, k] == pytest.approx(want, rel=1e-15)
+    assert 0 < clamped < len(S)  # both branches of the clamp are exercised
     # the inputs have unit rms
     np.testing.assert_allclose(np.sqrt(np.mean(X[:, :15] ** 2, axis=1)), 1.0, rtol=1e-12)
     assert np.all(X[:, 15] == 0)
@@ -151,3 +156,23 @@ def test_targets_are_the_streamed_in_values_of_a_periodic_grid():
     want = oracle.step("D2Q5", (nx, ny, 1), tau, g, 1)
     got = oracle.step("D2Q5", (nx, ny, 1), tau, g, 1, bc="open_ghost", ghost=ghost)
     np.testing.assert_allclose(got, want, atol=1e-14)
+
+
+def test_clamped_learned_edge_never_adds_weighted_energy():
+    """With the passivity clamp, even a random (untrained, large) network cannot make the weighted
+    energy grow on an open grid at tau >= 1/2: the edge injects at most what leaves."""
+    s = oracle.velset("D2Q5")
+    nx, ny = 14, 11
+    rng = np.random.default_rng(13)
+    g = rng.normal(size=(5, nx * ny))
+    p = mlp.init_params(14) * 8.0  # deliberately wild weights
+    for tau in (0.5, 0.6, 1.3):
+        e_prev = oracle.reduce("D2Q5", oracle.post_state("D2Q5", (nx, ny, 1), tau, g))[4]
+        gg = g
+        for _ in range(25):
+            post = oracle.post_state("D2Q5", (nx, ny, 1), tau, gg)
+            ghost = mlp.ghost_values(p, post, (nx, ny, 1), s.c, s.f)
+            gg = oracle.step("D2Q5", (nx, ny, 1), tau, gg, 1, bc="open_ghost", ghost=ghost)
+            e = oracle.reduce("D2Q5", oracle.post_state("D2Q5", (nx, ny, 1), tau, gg))[4]
+            assert e <= e_prev * (1 + 1e-12), (tau, e, e_prev)
+            e_prev = e
