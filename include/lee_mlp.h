@@ -11,11 +11,12 @@
  *            values S g_i / f*_i are used as they are),
  *   s      = max(rms(h), 1e-30),  x = (h / s, 0)  (16 values),
  *   y      = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3,   GELU(z) = z (1 + erf(z / sqrt 2)) / 2,
- *   g_in   = clamp(s * y, -|h_out|, |h_out|) * f*_in   (without the f*_in factor for 16-bit
- *            storage, in stored units), h_out = the outward population leaving through the same
- *            edge cell (strip slot 2 at depth 0).  The clamp makes the edge passive: it never
- *            adds weighted energy sum g^2 / f*, so with tau >= 1/2 the step is L2-stable for any
- *            network weights.
+ *   g_in   = a s y f*_in   (a s y for 16-bit storage, in stored units).  The factor a <= 1 is
+ *            the passivity bound of each group of 16 consecutive border rows (rows ordered x = 0,
+ *            x = nx - 1, y = 0, y = ny - 1, then along the edge): a = min(1, sqrt(sum h_out^2 /
+ *            sum (s y)^2)) over the group, h_out the outward population leaving through the same
+ *            cell (strip slot 2 at depth 0).  The edge then never adds weighted energy
+ *            sum g^2 / f*, so with tau >= 1/2 the step is L2-stable for any network weights.
  * Sizes 16 -> 64 -> 64 -> 1.  The GEMMs run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
  * FP32 accumulation): weights and every layer input are rounded to BF16, biases stay FP32.
  *

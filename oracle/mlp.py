@@ -196,10 +196,14 @@ def targets(post, shape, c, f, region):
     return np.array(T) / S
 
 
+SEGMENT = 16  # border rows per passivity group (one warp's rows on the GPU)
+
+
 def ghost_values(p, post, shape, c, f, quantize: bool = True):
     """Entering populations of the four edges of a whole open grid predicted by the network,
-    clamped to the magnitude of the outward population leaving through the same edge cell:
-    ghost[4][L] (L = max(nx, ny)) in solver units, the layout of the ghost-fed open step."""
+    passivity-bounded per group of 16 consecutive border rows (edges in the order x = 0,
+    x = nx - 1, y = 0, y = ny - 1): ghost[4][L] (L = max(nx, ny)) in solver units, the layout of
+    the ghost-fed open step."""
     nx, ny = shape[0], shape[1]
     region = (0, 0, nx, ny)
     X, S, E, P = strips(post, shape, c, f, region)
@@ -207,10 +211,15 @@ def ghost_values(p, post, shape, c, f, quantize: bool = True):
     idx = {(int(ci[0]), int(ci[1])): i for i, ci in enumerate(c)}
     L = max(nx, ny)
     ghost = np.zeros((4, L))
-    for xv, yv, s, e, k in zip(X, y, S, E, P):
-        # passivity clamp: |entering| <= |outward population leaving through the same edge
-        # cell| (strip slot 2 at depth 0), in units of f*; both are moving velocities with the
-        # same weight, so the edge cannot add weighted energy
-        hout = abs(xv[2] * s)
-        ghost[e, k] = min(max(s * yv, -hout), hout) * f[idx[CANON[e][1]]]
+    vin = S * y                 # entering populations in units of f*
+    hout = X[:, 2] * S          # outward populations leaving through the same cells
+    # passivity bound per group of 16 consecutive border rows: if the entering weighted energy
+    # exceeds the leaving one, the group's entering populations are scaled down together
+    for g0 in range(0, len(vin), SEGMENT):
+        sl = slice(g0, g0 + SEGMENT)
+        ein, eout = float(np.sum(vin[sl] ** 2)), float(np.sum(hout[sl] ** 2))
+        if ein > eout:
+            vin[sl] *= math.sqrt(eout / ein)
+    for v, e, k in zip(vin, E, P):
+        ghost[e, k] = v * f[idx[CANON[e][1]]]
     return ghost

@@ -427,6 +427,27 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const
     MlpFwd F;
     mlp_forward_warp(W, ax, F);
     const int gq = lane >> 2, t = lane & 3;
+    // Passivity bound over the warp's 16 border cells: the entering populations may carry at most
+    // the weighted energy sum g^2 / f* of the outward populations leaving through the same cells
+    // (canonical slot 2 at depth 0 of each strip; entering and leaving velocities share f*).  If
+    // the network's predictions exceed it they are scaled down together.  The edge then never adds
+    // weighted energy, so with tau >= 1/2 the whole step is L2-stable whatever the network predicts.
+    float vin[2], ein = 0.f, eout = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int lr = gq + 8 * h;
+        const bool ok = (t == 0) && (row0 + lr < R);
+        const float hout = tile[warp][lr][2] * sc[warp][lr];
+        vin[h] = ok ? sc[warp][lr] * (h ? F.y_hi : F.y_lo) : 0.f;
+        ein += vin[h] * vin[h];
+        eout += ok ? hout * hout : 0.f;
+    }
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        ein += __shfl_xor_sync(0xffffffffu, ein, off);
+        eout += __shfl_xor_sync(0xffffffffu, eout, off);
+    }
+    const float factor = ein > eout ? sqrtf(eout / ein) : 1.f;
     if (t == 0) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -435,13 +456,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const
             if (r < R) {
                 const EdgeRow E = edge_row(r, 0, 0, NX, NY);
                 const int iin = c_canon[E.e][1];
-                // Passivity clamp: the entering population may not exceed in magnitude the
-                // outward population leaving through the same edge cell (canonical slot 2 at
-                // depth 0 of the strip, same weight f*).  Then the edge never adds weighted
-                // energy sum g^2 / f*, and with tau >= 1/2 the whole step is L2-stable whatever
-                // the network predicts.
-                const float hout = fabsf(tile[warp][lr][2] * sc[warp][lr]);
-                float v = fminf(fmaxf(sc[warp][lr] * (h ? F.y_hi : F.y_lo), -hout), hout);
+                float v = vin[h] * factor;
                 if (!Store<T>::scaled) v /= inv_f(iin);
                 ghost[E.e * L + E.k] = (C)v;
             }

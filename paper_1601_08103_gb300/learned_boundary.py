@@ -35,34 +35,44 @@ def _torch():
 
 def training_domains(batch: int, region: int, rng):
     """Pulse specs of one batch: 1-3 Gaussians per domain with centres inside the physical
-    region, amplitude ~ U[1e-4, 1e-3], width ~ U[4, 24] cells."""
+    region, amplitude ~ U[1e-4, 1e-3], width ~ U[region / 32, region / 6] cells."""
     specs = []
     for _ in range(batch):
         k = int(rng.integers(1, 4))
         pulses = [(rng.uniform(region, 2 * region), rng.uniform(region, 2 * region), rng.uniform(1e-4, 1e-3),
-                   rng.uniform(4.0, 24.0)) for _ in range(k)]
+                   rng.uniform(region / 32.0, region / 6.0)) for _ in range(k)]
         specs.append(pulses)
     return specs
 
 
-def domain_fields(pulses, n):
-    rho = np.zeros(n * n)
+def _pulse_fields_on_device(pulses, n):
+    """Density of the pulses on an n x n periodic grid (minimum-image distances), built on the
+    device; zero velocity and temperature perturbations."""
+    torch = _torch()
+    ax = torch.arange(n, dtype=torch.float64, device="cuda")
+    rho = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     for cx, cy, a, w in pulses:
-        rho += inputs.gaussian_pulse((n, n, 1), a, w, (cx, cy, 0))
-    u, th = inputs.zero_rest(2, n * n)
-    return rho, u, th
+        dx = torch.remainder(ax - cx + n / 2.0, n) - n / 2.0
+        dy = torch.remainder(ax - cy + n / 2.0, n) - n / 2.0
+        rho += a * torch.exp(-(dy[:, None] ** 2 + dx[None, :] ** 2) / (w * w))
+    zeros_u = torch.zeros((2, n * n), dtype=torch.float64, device="cuda")
+    zeros_t = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    return rho.reshape(-1), zeros_u, zeros_t
 
 
-def generate_samples(lee, trajectories: int = 5000, region: int = 128, steps: int = 256, record_every: int = 4,
+def generate_samples(lee, trajectories: int = 5000, region: int = 256, steps: int = 512, record_every: int = 8,
                      batch: int = 96, tau: float = 0.6, seed: int = 5, min_scale: float = 1e-9, stream=None):
     """Runs `trajectories` seeded pulse runs on 3x enlarged periodic domains (FP32, batched, one
     CUDA graph per run length) and returns device tensors (x[rows][16], t[rows]) of border
-    samples whose strip scale exceeds `min_scale` (strips the pulse has not reached carry no
-    information)."""
+    samples.  Strips the pulse has not reached (scale below `min_scale`) are dropped, and the
+    rest are kept with probability min(1, (s / s90)^2), s90 the 90th percentile of the record's
+    scales, which weights the set towards the strips that carry the wave's energy."""
     torch = _torch()
     assert steps <= 2 * region, "waves would wrap around the enlarged box"
     n = 3 * region
     rng = np.random.default_rng(seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
     R = 4 * region
     xs, ts = [], []
     done = 0
@@ -71,14 +81,18 @@ def generate_samples(lee, trajectories: int = 5000, region: int = 128, steps: in
         specs = training_domains(count, region, rng)
         with lee.Batch("D2Q5", "f32", [(n, n, tau)] * count, stream=stream) as b:
             for d, pulses in enumerate(specs):
-                b.init_fields(d, *(torch.from_numpy(a).cuda() for a in domain_fields(pulses, n)))
+                b.init_fields(d, *_pulse_fields_on_device(pulses, n))
             xb = torch.empty((count * R, 16), device="cuda")
             tb = torch.empty(count * R, device="cuda")
             sb = torch.empty(count * R, device="cuda")
             for t in range(0, steps, record_every):
                 b.step(record_every, "graph")
                 lee.lee_batch_edge_samples(b.b, region, region, region, region, xb, tb, sb)
-                keep = sb > min_scale
+                live = sb > min_scale
+                if not bool(live.any()):
+                    continue
+                s90 = torch.quantile(sb[live][: 1 << 20], 0.9)
+                keep = live & (torch.rand(sb.shape, device="cuda", generator=gen) < (sb / s90) ** 2)
                 xs.append(xb[keep].clone())
                 ts.append(tb[keep].clone())
         done += count
