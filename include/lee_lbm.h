@@ -125,7 +125,10 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  * collision kernel per step (plus the boundary network for OPEN_LEARNED).  Asynchronous.  For
  * n >= 8 the launches are replayed from a CUDA graph (one graph holding all n steps for
  * n <= 4096, else repeated 100-step graphs), captured on first use of that length on a private
- * stream and cached in the handle; results are identical to direct launches. */
+ * stream and cached in the handle; results are identical to direct launches.  A 1D grid whose
+ * two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB, e.g. D1Q3 FP64 up
+ * to 4843 cells) runs all n >= 2 steps in one launch of a single-block kernel instead, again
+ * with identical results. */
 lee_status lee_lbm_step(lee_lbm *h, int64_t n);
 
 /* Per-cell moments of the current state (Sec. 4 discrete moments; Sec. 5 temperature for

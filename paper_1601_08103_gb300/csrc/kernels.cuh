@@ -356,6 +356,49 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
     }
 }
 
+// All n steps of a small 1D grid in one launch: one block keeps both population copies in
+// shared memory (in the storage type, so every step rounds exactly like the global-memory path)
+// and synchronises between steps.  Same per-cell arithmetic as k_stream_collide, so the result
+// equals n launches of it bit for bit.  The final state is written back to g (in place).
+template <class S, class T>
+__global__ void __launch_bounds__(1024) k_onchip_1d(T *__restrict__ g, int nx, long long pitch,
+                                                    CollideCoef<typename Store<T>::C> cf,
+                                                    OpenEdge<typename Store<T>::C> ob, bool open, long long nsteps) {
+    using C = typename Store<T>::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bufA = reinterpret_cast<T *>(smem_raw);
+    T *bufB = bufA + (size_t)S::Q * nx;
+    for (int k = threadIdx.x; k < S::Q * nx; k += blockDim.x) bufA[k] = g[(long long)(k / nx) * pitch + k % nx];
+    __syncthreads();
+    const GridDesc gd{nx, 1, 1, nx, nx, nx};
+    for (long long step = 0; step < nsteps; ++step) {
+        const T *src = (step & 1) ? bufB : bufA;
+        T *dst = (step & 1) ? bufA : bufB;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            C pull[S::Q][1], post[S::Q][1];
+            static_for<S::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                int xs = x - S::c(i, 0);
+                bool out = false;
+                if (xs < 0) { if (open) out = true; else xs += nx; }
+                if (xs >= nx) { if (open) out = true; else xs -= nx; }
+                pull[i][0] = out ? C(0) : Store<T>::load(src[i * nx + xs]);
+            });
+            collide_cell<S, 0>(pull, post, cf);
+            if (open && ob.sponge_w > 0) {
+                const C damp = sponge_factor<C>(x, 0, 0, gd, 1, ob.sponge_w, ob.sponge_smax);
+#pragma unroll
+                for (int i = 0; i < S::Q; ++i) post[i][0] *= damp;
+            }
+#pragma unroll
+            for (int i = 0; i < S::Q; ++i) dst[i * nx + x] = Store<T>::make(post[i][0]);
+        }
+        __syncthreads();
+    }
+    const T *fin = (nsteps & 1) ? bufB : bufA;
+    for (int k = threadIdx.x; k < S::Q * nx; k += blockDim.x) g[(long long)(k / nx) * pitch + k % nx] = fin[k];
+}
+
 // One fused time step on one grid: one thread per V-cell chunk.
 template <class S, class T, int V, bool OPEN>
 __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,

@@ -348,6 +348,14 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         return h->ops->step(L);
     };
     int64_t left = n;
+    // 1D grids that fit in shared memory: every step in one launch of the on-chip kernel
+    if (h->ops->onchip_1d && n >= 2 &&
+        2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem) {
+        L.stream = h->st;
+        LEE_CK(h, h->ops->onchip_1d(L, h->buf[h->cur], n), "on-chip 1D launch");
+        h->steps += n;
+        return LEE_OK;
+    }
     if (n >= kGraphMinSteps) {
         // Runs of up to kMaxGraphSteps steps are one launch of a graph holding all of them;
         // longer runs replay a kChunkGraphSteps graph.  Graphs have an even number of steps, so

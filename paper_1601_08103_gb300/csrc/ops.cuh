@@ -48,6 +48,9 @@ struct SetOps {
                               cudaStream_t st);
     cudaError_t (*import_f64)(int storage, const double *in, long long cells, long long pitch, const SetConsts &k, void *g,
                               cudaStream_t st);
+    // all steps of a small 1D grid in one launch, in place on g (nullptr for 2D/3D sets);
+    // returns cudaErrorInvalidValue when the grid does not fit in shared memory
+    cudaError_t (*onchip_1d)(const StepLaunch &L, void *g, long long nsteps);
     // sponge-frame damping of a stored state (after init_fields)
     cudaError_t (*sponge_damp)(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
                                cudaStream_t st);
@@ -77,6 +80,9 @@ CollideCoef<C> make_coef(double omega, const double M[4][4], const double N[4][4
         }
     return cf;
 }
+
+// Largest dynamic shared memory a block may use on this GPU (227 KB on sm_103a).
+constexpr int kMaxOnchipSmem = 227 * 1024;
 
 // Host-side velocity-set constants (the same compile-time tables the kernels use).
 template <class S>

@@ -120,6 +120,27 @@ struct SetImpl {
             return cudaGetLastError();
         });
     }
+    static cudaError_t onchip_1d(const StepLaunch &L, void *g, long long nsteps) {
+        if constexpr (S::D != 1) {
+            return cudaErrorInvalidValue;
+        } else {
+            return with_storage(L.storage, [&](auto *tp) {
+                using T = std::remove_pointer_t<decltype(tp)>;
+                using C = typename Store<T>::C;
+                const size_t smem = 2 * sizeof(T) * (size_t)S::Q * (size_t)L.nx;
+                if (smem > (size_t)kMaxOnchipSmem) return cudaErrorInvalidValue;
+                cudaError_t e = cudaFuncSetAttribute(k_onchip_1d<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
+                OpenEdge<C> ob{L.sponge_w, (C)L.sponge_smax, nullptr, 0};
+                const int threads = L.nx < 1024 ? ((L.nx + 31) / 32) * 32 : 1024;
+                k_onchip_1d<S, T><<<1, threads, smem, L.stream>>>(static_cast<T *>(g), L.nx, L.pitch, cf, ob, L.open,
+                                                                  nsteps);
+                return cudaGetLastError();
+            });
+        }
+    }
     static SetOps make() {
         SetOps o{};
         o.D = S::D;
@@ -132,6 +153,7 @@ struct SetImpl {
         o.export_f64 = &export_f64;
         o.import_f64 = &import_f64;
         o.sponge_damp = &sponge_damp;
+        o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);

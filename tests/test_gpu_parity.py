@@ -254,14 +254,17 @@ def test_full_size_2d_config_against_oracle(gpu_lib):
     assert_close(mr, want, 1e-12, "2D config rho'")
 
 
-@pytest.mark.parametrize("name,shape,storage,bc", [("D2Q5", (260, 37, 1), "f32", "periodic"),
+@pytest.mark.parametrize("name,shape,storage,bc", [("D1Q3", (1024, 1, 1), "f64", "periodic"),
+                                                    ("D1Q3", (1000, 1, 1), "f16", "open_sponge"),
+                                                    ("D2Q5", (260, 37, 1), "f32", "periodic"),
                                                     ("D3Q7", (36, 10, 7), "f16", "periodic"),
                                                     ("D2Q5", (64, 48, 1), "f64", "open_sponge"),
                                                     ("D2Q5", (64, 48, 1), "f32", "open_learned")])
 def test_graph_replay_equals_direct_launches(gpu_lib, name, shape, storage, bc):
-    """lee_lbm_step(n) replays captured graphs for n >= 8; the result equals n single steps bit
-    for bit, for whole-run graphs (n <= 4096, odd n leaves one direct step) and for chunked
-    replays (n > 4096)."""
+    """lee_lbm_step(n) replays captured graphs for n >= 8 (1D grids that fit on chip: one
+    single-block launch for all n steps); the result equals n single steps bit for bit, for
+    whole-run graphs (n <= 4096, odd n leaves one direct step) and for chunked replays
+    (n > 4096)."""
     lee = gpu_lib
     from oracle import mlp as omlp
 
@@ -286,3 +289,19 @@ def test_graph_replay_equals_direct_launches(gpu_lib, name, shape, storage, bc):
                 sv.get_populations(g)
                 outs.append(g)
         assert np.array_equal(outs[0], outs[1]), n
+
+
+def test_1d_config_matches_oracle_and_dalembert(gpu_lib):
+    """The 1D configuration (D1Q3, N = 1024, FP64, tau = 0.8, Gaussian pulse amplitude 1e-3 width
+    20 at a seeded centre, 2000 steps) on the GPU: within 1e-12 of the oracle and at rounding
+    level of the closed-form d'Alembert solution (Sec. 9.1)."""
+    lee = gpu_lib
+    rho, u, th = inputs.config_1d(1024, seed=1)
+    with lee.Solver("D1Q3", (1024, 1, 1), 0.8, storage="f64") as sv:
+        sv.init_fields(rho, u, th)
+        sv.step(2000)
+        r = np.empty(1024)
+        sv.moments(r)
+    g = oracle.step("D1Q3", (1024, 1, 1), 0.8, oracle.equilibrium("D1Q3", rho, u, th), 2000)
+    assert_close(r, oracle.moments("D1Q3", g)[0], 1e-12, "1D config vs oracle")
+    assert np.abs(r - an.dalembert_d1q3(rho, 2000)).max() <= 5e-13 * np.abs(rho).max()
