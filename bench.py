@@ -403,6 +403,8 @@ CASES = {
     "d2q5_f32_8192": ("D2Q5", (8192, 8192, 1), "f32", 0.6),
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
     "d3q7_f32_odd": ("D3Q7", (385, 383, 381), "f32", 0.55),
+    "d2q5_learned_1024": ("D2Q5", (1024, 1024, 1), "f32", 0.6, "open_learned"),
+    "d2q5_zero_1024": ("D2Q5", (1024, 1024, 1), "f32", 0.6, "open_zero"),
 }
 
 
@@ -414,7 +416,8 @@ def run_case(args):
     import paper_1601_08103_gb300 as lee
     from paper_1601_08103_gb300 import inputs
 
-    name, shape, storage, tau = CASES[args.case]
+    name, shape, storage, tau = CASES[args.case][:4]
+    bc = CASES[args.case][4] if len(CASES[args.case]) > 4 else "periodic"
     lee.load()
     stream = torch.cuda.current_stream()
     D = lee.lee_velset_info(name)["D"]
@@ -422,7 +425,11 @@ def run_case(args):
     c = [n / 2.7 for n in shape]
     rho = inputs.gaussian_pulse(shape, 1e-3, 16.0, c)
     u, th = inputs.zero_rest(D, cells)
-    with lee.Solver(name, shape, tau, storage=storage, stream=stream) as sv:
+    with lee.Solver(name, shape, tau, storage=storage, bc=bc, stream=stream) as sv:
+        if bc == "open_learned":
+            from paper_1601_08103_gb300 import learned_boundary
+
+            sv.set_boundary_mlp(learned_boundary.he_init(0))
         sv.init_fields(rho, u, th)
         sv.step(args.warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
