@@ -390,6 +390,18 @@ def forms_batched(steps: int = 1000):
             "speedup_launch_vs_sequential": round(seq / out["f32_launch"]["ms"], 3)}
 
 
+def forms_learned(n: int = 1024, steps: int = 3000):
+    """Learned-boundary form: the 1024^2 open D2Q5 grid (FP32, tau 0.6, seeded off-centre pulses,
+    3000 steps) with the zero-incoming edge, a 24-cell sponge frame (1072^2 grid) and the trained
+    boundary network shipped in paper_1601_08103_gb300/data, against the light-cone-enlarged FP64
+    periodic run: relative space-time L2 error of rho' and MLUPS per physical cell."""
+    import paper_1601_08103_gb300 as lee
+    from paper_1601_08103_gb300 import learned_boundary
+
+    params = np.load(os.path.join(ROOT, "paper_1601_08103_gb300", "data", "boundary_d2q5_tau0.6.npy"))
+    return learned_boundary.evaluate(lee, params.astype(np.float32), n=n, steps=steps)
+
+
 CASES = {
     # name: (set, shape, storage, tau)
     "d1q3_f64": ("D1Q3", (1024, 1, 1), "f64", 0.8),
@@ -506,6 +518,7 @@ def main(argv=None):
         if world == 1 and not args.no_forms:
             line["forms"] = forms_3d()
             line["forms_batched"] = forms_batched()
+            line["forms_learned"] = forms_learned()
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

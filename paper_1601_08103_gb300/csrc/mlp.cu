@@ -64,8 +64,9 @@ cudaError_t mlp_pack(const float *params_dev, void *packed, cudaStream_t st) {
 // ---------------------------------------------------------------------------------------------
 // inference on given inputs
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpDev W, const float *__restrict__ x, long long rows,
+__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpDev WG, const float *__restrict__ x, long long rows,
                                                                 float *__restrict__ y) {
+    __shared__ __align__(16) unsigned char wsm[kStagedWeightBytes];
     __shared__ float tile[kMlpWarps][16][kMlpIn];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long row0 = ((long long)blockIdx.x * kMlpWarps + warp) * 16;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_forward(MlpDev W, const 
         const long long r = row0 + e / kMlpIn;
         tile[warp][e / kMlpIn][e % kMlpIn] = r < rows ? x[r * kMlpIn + e % kMlpIn] : 0.f;
     }
-    __syncwarp();
+    const MlpDev W = stage_forward_weights(WG, wsm);  // ends with a block barrier
     uint32_t ax[4];
     a_frag_from_tile(tile[warp], ax);
     MlpFwd F;
@@ -399,15 +400,19 @@ __global__ void k_edge_inputs(const T *__restrict__ g, long long pitch, int NX, 
 
 // The learned boundary of one step: strips of the current post-collision state -> network ->
 // entering populations ghost[4][L] (arithmetic type C of the storage).
+constexpr int kBoundaryWarps = 2;  // small blocks: the 2 (nx + ny) border rows spread over many SMs
+
 template <class T>
-__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const T *__restrict__ g, long long pitch, int NX,
-                                                                 int NY, typename Store<T>::C *__restrict__ ghost, int L) {
+__global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG, const T *__restrict__ g, long long pitch,
+                                                                      int NX, int NY,
+                                                                      typename Store<T>::C *__restrict__ ghost, int L) {
     using C = typename Store<T>::C;
-    __shared__ float tile[kMlpWarps][16][kMlpIn];
-    __shared__ float sc[kMlpWarps][16];
+    __shared__ __align__(16) unsigned char wsm[kStagedWeightBytes];
+    __shared__ float tile[kBoundaryWarps][16][kMlpIn];
+    __shared__ float sc[kBoundaryWarps][16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = 2 * (NX + NY);
-    const int row0 = (blockIdx.x * kMlpWarps + warp) * 16;
+    const int row0 = (blockIdx.x * kBoundaryWarps + warp) * 16;
     if (lane < 16) {
         const int r = row0 + lane;
         float xv[kMlpIn], s = 1.f;
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_boundary(MlpDev W, const
         for (int k = 0; k < kMlpIn; ++k) tile[warp][lane][k] = xv[k];
         sc[warp][lane] = s;
     }
-    __syncwarp();
+    const MlpDev W = stage_forward_weights(WG, wsm);  // ends with a block barrier
     uint32_t ax[4];
     a_frag_from_tile(tile[warp], ax);
     MlpFwd F;
@@ -480,12 +485,12 @@ cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, 
                                 int L, cudaStream_t st) {
     const MlpDev W = mlp_dev(packed);
     const int R = 2 * (NX + NY);
-    const int blocks = (R + kChunkRows - 1) / kChunkRows;
+    const int blocks = (R + 16 * kBoundaryWarps - 1) / (16 * kBoundaryWarps);
     return with_store(storage, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         using C = typename Store<T>::C;
-        k_mlp_boundary<T><<<blocks, 32 * kMlpWarps, 0, st>>>(W, static_cast<const T *>(g), pitch, NX, NY,
-                                                             static_cast<C *>(ghost), L);
+        k_mlp_boundary<T><<<blocks, 32 * kBoundaryWarps, 0, st>>>(W, static_cast<const T *>(g), pitch, NX, NY,
+                                                                  static_cast<C *>(ghost), L);
         return cudaGetLastError();
     });
 }

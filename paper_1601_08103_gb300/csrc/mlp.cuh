@@ -59,8 +59,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
-// Two consecutive BF16 values of a weight row as one 32-bit word (read-only path).
-__device__ __forceinline__ uint32_t ldw(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+// Two consecutive BF16 values of a weight row as one 32-bit word (generic address: the weights
+// may sit in global or in shared memory).
+__device__ __forceinline__ uint32_t ldw(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned int *>(p); }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -85,7 +86,7 @@ __device__ __forceinline__ void mlp_forward_warp(const MlpDev &W, const uint32_t
         F.z1[j][0] = F.z1[j][1] = F.z1[j][2] = F.z1[j][3] = 0.f;
         const __nv_bfloat16 *w = W.w1 + (8 * j + g) * kMlpIn + 2 * t;
         mma16816(F.z1[j], ax, ldw(w), ldw(w + 8));
-        const float bb0 = __ldg(W.b1 + 8 * j + 2 * t), bb1 = __ldg(W.b1 + 8 * j + 2 * t + 1);
+        const float bb0 = W.b1[8 * j + 2 * t], bb1 = W.b1[8 * j + 2 * t + 1];
         F.z1[j][0] += bb0;
         F.z1[j][1] += bb1;
         F.z1[j][2] += bb0;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void mlp_forward_warp(const MlpDev &W, const uint32_t
             const __nv_bfloat16 *w = W.w2 + (8 * j + g) * kMlpHid + 16 * kk + 2 * t;
             mma16816(F.z2[j], a, ldw(w), ldw(w + 8));
         }
-        const float bb0 = __ldg(W.b2 + 8 * j + 2 * t), bb1 = __ldg(W.b2 + 8 * j + 2 * t + 1);
+        const float bb0 = W.b2[8 * j + 2 * t], bb1 = W.b2[8 * j + 2 * t + 1];
         F.z2[j][0] += bb0;
         F.z2[j][1] += bb1;
         F.z2[j][2] += bb0;
@@ -117,10 +118,34 @@ __device__ __forceinline__ void mlp_forward_warp(const MlpDev &W, const uint32_t
         const __nv_bfloat16 *w = W.w3 + g * kMlpHid + 16 * kk + 2 * t;
         mma16816(z3, a, ldw(w), ldw(w + 8));
     }
-    const float b3 = __ldg(W.b3);
+    const float b3 = W.b3[0];
     F.y_lo = z3[0] + b3;  // column 0 lives in lanes with t == 0
     F.y_hi = z3[2] + b3;
 }
+
+// Copies the forward weights (w1, w2, w3 and the biases: packed bytes [0, kPkW2T) and
+// [kPkW3, kMlpPackedBytes)) into a block's shared memory and returns views of them.  All threads
+// of the block must call it; it ends with a barrier.
+__device__ __forceinline__ MlpDev stage_forward_weights(const MlpDev &G, unsigned char *smem) {
+    const uint4 *src0 = reinterpret_cast<const uint4 *>(G.w1);  // w1 | w2 are contiguous
+    uint4 *dst0 = reinterpret_cast<uint4 *>(smem);
+    for (int k = threadIdx.x; k < kPkW2T / 16; k += blockDim.x) dst0[k] = src0[k];
+    const uint4 *src1 = reinterpret_cast<const uint4 *>(G.w3);  // w3 | b1 | b2 | b3 are contiguous
+    uint4 *dst1 = reinterpret_cast<uint4 *>(smem + kPkW2T);
+    for (int k = threadIdx.x; k < (kMlpPackedBytes - kPkW3) / 16; k += blockDim.x) dst1[k] = src1[k];
+    __syncthreads();
+    MlpDev S;
+    S.w1 = reinterpret_cast<const __nv_bfloat16 *>(smem + kPkW1);
+    S.w2 = reinterpret_cast<const __nv_bfloat16 *>(smem + kPkW2);
+    S.w2t = G.w2t;  // not used by the forward pass
+    S.w3 = reinterpret_cast<const __nv_bfloat16 *>(smem + kPkW2T);
+    S.b1 = reinterpret_cast<const float *>(smem + kPkW2T + (kPkB1 - kPkW3));
+    S.b2 = reinterpret_cast<const float *>(smem + kPkW2T + (kPkB2 - kPkW3));
+    S.b3 = reinterpret_cast<const float *>(smem + kPkW2T + (kPkB3 - kPkW3));
+    return S;
+}
+// Shared memory that stage_forward_weights needs.
+constexpr int kStagedWeightBytes = kPkW2T + (kMlpPackedBytes - kPkW3);
 
 // A fragment of 16 rows x 16 inputs held in a row-major FP32 tile in shared memory.
 __device__ __forceinline__ void a_frag_from_tile(const float (*tile)[kMlpIn], uint32_t (&a)[4]) {
