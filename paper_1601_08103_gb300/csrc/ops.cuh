@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "kernels.cuh"
+#include "aux_kernels.cuh"
 
 namespace lee {
 
