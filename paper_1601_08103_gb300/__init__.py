@@ -69,6 +69,7 @@ _SIGS = {
     "lee_lbm_set_boundary_mlp": (ctypes.c_int, [_P, _P, _I64]),
     "lee_lbm_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "lee_lbm_store_scale": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
+    "lee_lbm_steps_per_launch": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "lee_lbm_sync": (ctypes.c_int, [_P]),
     "lee_lbm_last_error": (ctypes.c_char_p, [_P]),
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
@@ -247,6 +248,12 @@ def lee_lbm_steps_done(h) -> int:
     return v.value
 
 
+def lee_lbm_steps_per_launch(h) -> int:
+    v = _I32()
+    _check(_lib.lee_lbm_steps_per_launch(h, ctypes.byref(v)), "lee_lbm_steps_per_launch")
+    return v.value
+
+
 def lee_lbm_store_scale(h) -> float:
     v = _D()
     _check(_lib.lee_lbm_store_scale(h, ctypes.byref(v)), "lee_lbm_store_scale")
@@ -325,6 +332,10 @@ class Solver:
     @property
     def store_scale(self) -> float:
         return lee_lbm_store_scale(self.h)
+
+    @property
+    def steps_per_launch(self) -> int:
+        return lee_lbm_steps_per_launch(self.h)
 
     def sync(self):
         lee_lbm_sync(self.h)

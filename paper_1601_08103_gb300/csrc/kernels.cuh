@@ -407,6 +407,102 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
     stream_collide_chunk<S, T, V, OPEN>(src, dst, gd, cf, ob, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// ---------------------------------------------------------------------------------------------
+// two time steps per launch (temporal blocking) for periodic 2D grids
+// ---------------------------------------------------------------------------------------------
+// A block owns an output tile of kTbW columns x kTbH rows and marches down it row by row.  For
+// output row b it needs the intermediate state S(t+1) on rows b-1..b+1 and columns x0-1..x0+kTbW,
+// which in turn needs S(t) on rows b-2..b+2 and columns x0-2..x0+kTbW+1.  S(t) rows stream in
+// through an 8-row shared-memory ring (cp.async, kTbPrefetch rows ahead); S(t+1) rows live in a
+// 4-row ring in the storage type, so every value is rounded exactly as in two single steps and
+// the result equals them bit for bit.  DRAM sees one read and one write of every population per
+// two steps (plus 4 halo rows per tile, mostly served by L2 because neighbouring tiles run
+// together).
+constexpr int kTbW = 128, kTbH = 32, kTbPrefetch = 4;
+constexpr int kTbLoadW = kTbW + 4, kTbMidW = kTbW + 2;
+
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <class S, class T>
+__global__ void __launch_bounds__(kTbW) k_stream_collide_2step(const T *__restrict__ src, T *__restrict__ dst, int nx,
+                                                               int ny, long long pitch,
+                                                               CollideCoef<typename Store<T>::C> cf) {
+    static_assert(S::D == 2, "two-step tiles are 2D");
+    static_assert(sizeof(T) == 4, "FP32 storage (the rings of wider types exceed static shared memory)");
+    using C = typename Store<T>::C;
+    __shared__ T r0[8][S::Q][kTbLoadW];  // S(t), ring indexed by load iteration & 7
+    __shared__ T r1[4][S::Q][kTbMidW];   // S(t+1), ring indexed by iteration & 3
+    const int j = threadIdx.x;
+    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * kTbH;
+    const int iters = kTbH + 4;
+
+    // Issues the loads of S(t) row y0 - 2 + k (columns x0-2 .. x0+kTbW+1, periodic) into slot k & 7.
+    auto load_row = [&](int k) {
+        if (k < iters) {
+            int r = (y0 - 2 + k) % ny;
+            if (r < 0) r += ny;
+            const long long rowoff = (long long)r * nx;
+            for (int c = j; c < kTbLoadW; c += kTbW) {
+                int x = x0 - 2 + c;
+                if (x < 0) x += nx;
+                if (x >= nx) x -= nx;
+#pragma unroll
+                for (int i = 0; i < S::Q; ++i) cp_async_4(&r0[k & 7][i][c], src + (long long)i * pitch + rowoff + x);
+            }
+        }
+        cp_async_commit();  // one group per iteration, empty past the end, keeps the wait count fixed
+    };
+
+#pragma unroll
+    for (int k = 0; k < kTbPrefetch; ++k) load_row(k);
+
+    for (int k = 0; k < iters; ++k) {
+        load_row(k + kTbPrefetch);
+        cp_async_wait<kTbPrefetch>();
+        __syncthreads();  // row k of S(t) visible to all threads
+        if (k >= 2) {
+            // step t -> t+1 on row a = y0 - 3 + k, columns x0-1 .. x0+kTbW (local c = 0 .. kTbW+1)
+            for (int c = j; c < kTbMidW; c += kTbW) {
+                C pull[S::Q][1], post[S::Q][1];
+                static_for<S::Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                    // S(t) row a - cy = load iteration k - 1 - cy, column (x - cx) -> local c + 1 - cx
+                    pull[i][0] = Store<T>::load(r0[(k - 1 - cy) & 7][i][c + 1 - cx]);
+                });
+                collide_cell<S, 0>(pull, post, cf);
+#pragma unroll
+                for (int i = 0; i < S::Q; ++i) r1[k & 3][i][c] = Store<T>::make(post[i][0]);
+            }
+        }
+        __syncthreads();  // row a of S(t+1) visible; the oldest S(t) row may be overwritten
+        if (k >= 4) {
+            // step t+1 -> t+2 on row b = y0 - 4 + k, columns x0 .. x0+kTbW-1
+            const int b = y0 - 4 + k;
+            C pull[S::Q][1], post[S::Q][1];
+            static_for<S::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                // S(t+1) row b - cy was produced at iteration k - 1 - cy; column (x - cx) -> j + 1 - cx
+                pull[i][0] = Store<T>::load(r1[(k - 1 - cy) & 3][i][j + 1 - cx]);
+            });
+            collide_cell<S, 0>(pull, post, cf);
+            if (b < ny) {
+                T *outp = dst + (long long)b * nx + x0 + j;
+#pragma unroll
+                for (int i = 0; i < S::Q; ++i) outp[(long long)i * pitch] = Store<T>::make(post[i][0]);
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
 // blocks [first_block[d], first_block[d+1]); its populations start at element offset[d] of the
 // shared buffers, and it has its own extents and relaxation coefficients (its own tau).  The

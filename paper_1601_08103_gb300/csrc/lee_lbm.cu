@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -241,6 +242,7 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     h->pitch = (cells + 63) / 64 * 64;
     h->elem = elem_size(cfg->storage);
     h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+    if (const char *ev = std::getenv("LEE_SINGLE_STEP")) h->single_step_only = ev[0] == '1';
     const bool is16 = cfg->storage == LEE_STORE_F16 || cfg->storage == LEE_STORE_BF16;
     h->scale = is16 ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -356,14 +358,29 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         h->steps += n;
         return LEE_OK;
     }
-    if (n >= kGraphMinSteps) {
+    // Periodic 2D FP32 grids whose width is a multiple of the tile: two steps per launch
+    // (temporal blocking; bit-identical to two single steps).
+    const bool two = h->ops->step2 && !L.open && h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 128 == 0 &&
+                     h->cfg.ny >= 3 && !h->single_step_only;
+    const int unit = two ? 2 : 1;
+    auto launch_unit = [&](int from, cudaStream_t st) -> cudaError_t {
+        if (!two) return launch_step(from, st);
+        L.src = h->buf[from];
+        L.dst = h->buf[from ^ 1];
+        L.stream = st;
+        return h->ops->step2(L);
+    };
+    int64_t units = n / unit;
+    if (units * unit >= kGraphMinSteps) {
         // Runs of up to kMaxGraphSteps steps are one launch of a graph holding all of them;
-        // longer runs replay a kChunkGraphSteps graph.  Graphs have an even number of steps, so
-        // a replay leaves the buffer parity unchanged; they are captured once per (parity,
+        // longer runs replay a kChunkGraphSteps graph.  Graphs hold an even number of launches,
+        // so a replay leaves the buffer parity unchanged; they are captured once per (parity,
         // length) on a private stream and replayed on the handle's stream.
-        const long long glen = n <= kMaxGraphSteps ? (n & ~1LL) : kChunkGraphSteps;
-        while (left >= glen) {
-            auto it = h->exec.find({h->cur, glen});
+        const long long gunits =
+            units * unit <= kMaxGraphSteps ? (units & ~1LL) : (kChunkGraphSteps / unit) & ~1LL;
+        while (gunits > 0 && units >= gunits) {
+            const long long gsteps = gunits * unit;
+            auto it = h->exec.find({h->cur, gsteps});
             cudaGraphExec_t ex = it == h->exec.end() ? nullptr : it->second;
             if (!ex) {
                 if (!h->cap) LEE_CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
@@ -371,19 +388,25 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
                 LEE_CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
                 cudaError_t e = cudaSuccess;
                 int w = h->cur;
-                for (long long k = 0; k < glen && e == cudaSuccess; ++k, w ^= 1) e = launch_step(w, h->cap);
+                for (long long k = 0; k < gunits && e == cudaSuccess; ++k, w ^= 1) e = launch_unit(w, h->cap);
                 cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
                 if (e == cudaSuccess) e = e2;
                 if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
                 if (g) cudaGraphDestroy(g);
                 LEE_CK(h, e, "step graph capture");
-                h->exec[{h->cur, glen}] = ex;
+                h->exec[{h->cur, gsteps}] = ex;
             }
             LEE_CK(h, cudaGraphLaunch(ex, h->st), "step graph launch");
-            left -= glen;
-            h->steps += glen;
+            units -= gunits;
+            h->steps += gsteps;
         }
     }
+    for (; units > 0; --units) {
+        LEE_CK(h, launch_unit(h->cur, h->st), "step launch");
+        h->cur ^= 1;
+        h->steps += unit;
+    }
+    left = n % unit;
     for (; left > 0; --left) {
         LEE_CK(h, launch_step(h->cur, h->st), "step launch");
         h->cur ^= 1;
@@ -495,6 +518,15 @@ lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t npa
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
     *steps = h->steps;
+    return LEE_OK;
+}
+
+lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps) {
+    if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
+    const bool two = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
+                     h->cfg.nx % 128 == 0 && h->cfg.ny >= 3 && !h->single_step_only;
+    const bool onchip = h->ops->onchip_1d && 2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
+    *steps = onchip ? 0 : (two ? 2 : 1);
     return LEE_OK;
 }
 

@@ -33,6 +33,9 @@ struct SetOps {
     int D, Q;
     // one fused pull-stream + collide step
     cudaError_t (*step)(const StepLaunch &);
+    // two fused steps per launch (periodic 2D FP32 grids with nx % 128 == 0; nullptr otherwise):
+    // reads L.src, writes the state two steps later into L.dst
+    cudaError_t (*step2)(const StepLaunch &);
     // g = g^eq(fields) (fields FP64 on device)
     cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                         long long pitch, const SetConsts &k, cudaStream_t st);

@@ -141,6 +141,19 @@ struct SetImpl {
             });
         }
     }
+    static cudaError_t step2(const StepLaunch &L) {
+        if constexpr (S::D != 2) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (L.storage != LEE_STORE_F32 || L.open || L.nx % kTbW != 0 || L.ny < 3) return cudaErrorInvalidValue;
+            const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
+            const dim3 grid(L.nx / kTbW, (L.ny + kTbH - 1) / kTbH);
+            k_stream_collide_2step<S, float><<<grid, kTbW, 0, L.stream>>>(static_cast<const float *>(L.src),
+                                                                          static_cast<float *>(L.dst), L.nx, L.ny,
+                                                                          L.pitch, cf);
+            return cudaGetLastError();
+        }
+    }
     static SetOps make() {
         SetOps o{};
         o.D = S::D;
@@ -154,6 +167,7 @@ struct SetImpl {
         o.import_f64 = &import_f64;
         o.sponge_damp = &sponge_damp;
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
+        o.step2 = S::D == 2 ? &step2 : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);
