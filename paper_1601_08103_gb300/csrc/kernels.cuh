@@ -408,95 +408,139 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 }
 
 // ---------------------------------------------------------------------------------------------
-// two time steps per launch (temporal blocking) for periodic 2D grids
+// two time steps per launch (temporal blocking) for periodic 2D FP32 grids
 // ---------------------------------------------------------------------------------------------
-// A block owns an output tile of kTbW columns x kTbH rows and marches down it row by row.  For
-// output row b it needs the intermediate state S(t+1) on rows b-1..b+1 and columns x0-1..x0+kTbW,
-// which in turn needs S(t) on rows b-2..b+2 and columns x0-2..x0+kTbW+1.  S(t) rows stream in
-// through an 8-row shared-memory ring (cp.async, kTbPrefetch rows ahead); S(t+1) rows live in a
-// 4-row ring in the storage type, so every value is rounded exactly as in two single steps and
+// A block (4 warps) owns an output tile of kTbW = 128 columns x kTbH rows and marches down it
+// four rows per iteration, one row per warp, four cells (one float4) per lane.  Output row b at
+// t+2 needs S(t+1) on rows b-1..b+1 and columns x0-1..x0+128, which needs S(t) on rows b-2..b+2
+// and columns x0-2..x0+129.  Per iteration k (row blocks of 4):
+//   L_k: S(t) rows y0-2+4k .. y0+1+4k stream in by 16-byte cp.async, kTbPrefetch blocks ahead,
+//        into a 4-block ring (columns x0-4 .. x0+131, so every chunk is 16-byte aligned);
+//   A_k: S(t+1) rows y0+4k-5 .. y0+4k-2 from L_{k-1}, L_k into a 3-block ring;
+//   B_k: S(t+2) rows y0+4k-12 .. y0+4k-9 from A_{k-2}, A_{k-1}, stored to global memory.
+// B_k does not read A_k, so one barrier per iteration separates all producers and consumers.
+// S(t+1) is kept in the storage type, so every value is rounded exactly as in two single steps:
 // the result equals them bit for bit.  DRAM sees one read and one write of every population per
-// two steps (plus 4 halo rows per tile, mostly served by L2 because neighbouring tiles run
-// together).
-constexpr int kTbW = 128, kTbH = 32, kTbPrefetch = 4;
-constexpr int kTbLoadW = kTbW + 4, kTbMidW = kTbW + 2;
+// two steps, plus halo rows that neighbouring tiles (running at the same time) mostly take from L2.
+constexpr int kTbW = 128, kTbH = 32, kTbPrefetch = 2;
+constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+131
+constexpr int kTbR0 = 4, kTbR1 = 3;        // ring depths in 4-row blocks
 
-__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
+template <class S>
+constexpr int tb_smem_bytes() {
+    return (kTbR0 + kTbR1) * 4 * S::Q * kTbRow * (int)sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <class S, class T>
-__global__ void __launch_bounds__(kTbW) k_stream_collide_2step(const T *__restrict__ src, T *__restrict__ dst, int nx,
-                                                               int ny, long long pitch,
-                                                               CollideCoef<typename Store<T>::C> cf) {
-    static_assert(S::D == 2, "two-step tiles are 2D");
-    static_assert(sizeof(T) == 4, "FP32 storage (the rings of wider types exceed static shared memory)");
-    using C = typename Store<T>::C;
-    __shared__ T r0[8][S::Q][kTbLoadW];  // S(t), ring indexed by load iteration & 7
-    __shared__ T r1[4][S::Q][kTbMidW];   // S(t+1), ring indexed by iteration & 3
-    const int j = threadIdx.x;
-    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * kTbH;
-    const int iters = kTbH + 4;
+// Pulls the four cells of one lane for velocity i from a ring row (offsets relative to x0-4):
+// the lane's own float4 sits at 4*lane+4; c_x = +1 takes one element from the left neighbour
+// lane (or offset 3 for lane 0), c_x = -1 one from the right neighbour (or offset 132 for lane 31).
+template <int cx>
+__device__ __forceinline__ void tb_pull4(const float *row, int lane, float (&out)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * lane + 4);
+    if constexpr (cx == 0) {
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else if constexpr (cx == 1) {
+        float left = __shfl_up_sync(kFull, v.w, 1);
+        if (lane == 0) left = row[3];
+        out[0] = left; out[1] = v.x; out[2] = v.y; out[3] = v.z;
+    } else {
+        float right = __shfl_down_sync(kFull, v.x, 1);
+        if (lane == 31) right = row[132];
+        out[0] = v.y; out[1] = v.z; out[2] = v.w; out[3] = right;
+    }
+}
 
-    // Issues the loads of S(t) row y0 - 2 + k (columns x0-2 .. x0+kTbW+1, periodic) into slot k & 7.
-    auto load_row = [&](int k) {
-        if (k < iters) {
-            int r = (y0 - 2 + k) % ny;
+template <class S>
+__global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__restrict__ src, float *__restrict__ dst,
+                                                              int nx, int ny, long long pitch, CollideCoef<float> cf) {
+    static_assert(S::D == 2, "two-step tiles are 2D");
+    constexpr int Q = S::Q;
+    extern __shared__ __align__(16) float tb_smem[];
+    float *ring0 = tb_smem;                                // [kTbR0][4][Q][kTbRow]
+    float *ring1 = tb_smem + kTbR0 * 4 * Q * kTbRow;       // [kTbR1][4][Q][kTbRow]
+    auto r0 = [&](int blk, int w, int i) { return ring0 + (((blk % kTbR0) * 4 + w) * Q + i) * kTbRow; };
+    auto r1 = [&](int blk, int w, int i) { return ring1 + (((blk % kTbR1) * 4 + w) * Q + i) * kTbRow; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * kTbH;
+    const int iters = kTbH / 4 + 3;
+
+    // Block k of S(t): row y0 - 2 + 4k + warp, chunks of 4 columns starting at x0 - 4 (periodic).
+    auto load_block = [&](int k) {
+        const int row = y0 - 2 + 4 * k + warp;
+        if (row <= y0 + kTbH + 1) {
+            int r = row % ny;
             if (r < 0) r += ny;
             const long long rowoff = (long long)r * nx;
-            for (int c = j; c < kTbLoadW; c += kTbW) {
-                int x = x0 - 2 + c;
+            for (int c = lane; c < kTbRow / 4; c += 32) {
+                int x = x0 - 4 + 4 * c;
                 if (x < 0) x += nx;
                 if (x >= nx) x -= nx;
 #pragma unroll
-                for (int i = 0; i < S::Q; ++i) cp_async_4(&r0[k & 7][i][c], src + (long long)i * pitch + rowoff + x);
+                for (int i = 0; i < Q; ++i) cp_async_16(r0(k, warp, i) + 4 * c, src + (long long)i * pitch + rowoff + x);
             }
         }
-        cp_async_commit();  // one group per iteration, empty past the end, keeps the wait count fixed
+        cp_async_commit();  // one group per block (empty when nothing is needed)
     };
-
 #pragma unroll
-    for (int k = 0; k < kTbPrefetch; ++k) load_row(k);
+    for (int k = 0; k < kTbPrefetch; ++k) load_block(k);
 
     for (int k = 0; k < iters; ++k) {
-        load_row(k + kTbPrefetch);
-        cp_async_wait<kTbPrefetch>();
-        __syncthreads();  // row k of S(t) visible to all threads
-        if (k >= 2) {
-            // step t -> t+1 on row a = y0 - 3 + k, columns x0-1 .. x0+kTbW (local c = 0 .. kTbW+1)
-            for (int c = j; c < kTbMidW; c += kTbW) {
-                C pull[S::Q][1], post[S::Q][1];
-                static_for<S::Q>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                    // S(t) row a - cy = load iteration k - 1 - cy, column (x - cx) -> local c + 1 - cx
-                    pull[i][0] = Store<T>::load(r0[(k - 1 - cy) & 7][i][c + 1 - cx]);
-                });
-                collide_cell<S, 0>(pull, post, cf);
-#pragma unroll
-                for (int i = 0; i < S::Q; ++i) r1[k & 3][i][c] = Store<T>::make(post[i][0]);
-            }
-        }
-        __syncthreads();  // row a of S(t+1) visible; the oldest S(t) row may be overwritten
-        if (k >= 4) {
-            // step t+1 -> t+2 on row b = y0 - 4 + k, columns x0 .. x0+kTbW-1
-            const int b = y0 - 4 + k;
-            C pull[S::Q][1], post[S::Q][1];
-            static_for<S::Q>([&](auto I) {
+        cp_async_wait<kTbPrefetch - 1>();
+        __syncthreads();  // L_k complete and visible; A_{k-1} complete (read by B_k)
+        load_block(k + kTbPrefetch);  // ring slot (k+2) % 4: neither L_{k-1} nor L_k
+        // ---- A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + kTbH are not needed)
+        const int a = y0 + 4 * k - 5 + warp;
+        if (k >= 1 && a <= y0 + kTbH) {
+            float pull[Q][4], post[Q][4];
+            static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                // S(t+1) row b - cy was produced at iteration k - 1 - cy; column (x - cx) -> j + 1 - cx
-                pull[i][0] = Store<T>::load(r1[(k - 1 - cy) & 3][i][j + 1 - cx]);
+                const int rr = a - cy - (y0 - 2);  // row within the S(t) blocks
+                tb_pull4<cx>(r0(rr >> 2, rr & 3, i), lane, pull[i]);
             });
-            collide_cell<S, 0>(pull, post, cf);
-            if (b < ny) {
-                T *outp = dst + (long long)b * nx + x0 + j;
+            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pull, post, cf); });
 #pragma unroll
-                for (int i = 0; i < S::Q; ++i) outp[(long long)i * pitch] = Store<T>::make(post[i][0]);
+            for (int i = 0; i < Q; ++i)
+                *reinterpret_cast<float4 *>(r1(k, warp, i) + 4 * lane + 4) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
+            // the two halo columns of S(t+1): x0 - 1 (lane 0, offset 3) and x0 + 128 (lane 31, offset 132)
+            if (lane == 0 || lane == 31) {
+                const int off = lane == 0 ? 3 : 132;
+                float p1[Q][1], q1[Q][1];
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                    const int rr = a - cy - (y0 - 2);
+                    p1[i][0] = r0(rr >> 2, rr & 3, i)[off - cx];
+                });
+                collide_cell<S, 0>(p1, q1, cf);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) r1(k, warp, i)[off] = q1[i][0];
+            }
+        }
+        // ---- B_k: S(t+2) row b = y0 + 4k - 12 + warp from A_{k-2}, A_{k-1}
+        const int b = y0 + 4 * k - 12 + warp;
+        if (k >= 3 && b < y0 + kTbH) {
+            float pull[Q][4], post[Q][4];
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                const int rr = b - cy - (y0 - 5);  // row within the S(t+1) blocks
+                tb_pull4<cx>(r1(rr >> 2, rr & 3, i), lane, pull[i]);
+            });
+            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pull, post, cf); });
+            if (b < ny) {
+                float *outp = dst + (long long)b * nx + x0 + 4 * lane;
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    *reinterpret_cast<float4 *>(outp + (long long)i * pitch) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
             }
         }
     }

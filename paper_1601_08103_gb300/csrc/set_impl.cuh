@@ -147,10 +147,12 @@ struct SetImpl {
         } else {
             if (L.storage != LEE_STORE_F32 || L.open || L.nx % kTbW != 0 || L.ny < 3) return cudaErrorInvalidValue;
             const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
+            constexpr int smem = tb_smem_bytes<S>();
+            cudaError_t e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
             const dim3 grid(L.nx / kTbW, (L.ny + kTbH - 1) / kTbH);
-            k_stream_collide_2step<S, float><<<grid, kTbW, 0, L.stream>>>(static_cast<const float *>(L.src),
-                                                                          static_cast<float *>(L.dst), L.nx, L.ny,
-                                                                          L.pitch, cf);
+            k_stream_collide_2step<S><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
+                                                                     static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, cf);
             return cudaGetLastError();
         }
     }
