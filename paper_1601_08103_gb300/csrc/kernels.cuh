@@ -410,7 +410,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 // ---------------------------------------------------------------------------------------------
 // two time steps per launch (temporal blocking) for periodic 2D FP32 grids
 // ---------------------------------------------------------------------------------------------
-// A block (4 warps) owns an output tile of kTbW = 128 columns x kTbH rows and marches down it
+// A block (4 warps) owns an output tile of kTbW = 128 columns x H rows (H a multiple of 4, chosen
+// by the host so that all tiles are resident at once) and marches down it
 // four rows per iteration, one row per warp, four cells (one float4) per lane.  Output row b at
 // t+2 needs S(t+1) on rows b-1..b+1 and columns x0-1..x0+128, which needs S(t) on rows b-2..b+2
 // and columns x0-2..x0+129.  Per iteration k (row blocks of 4):
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 // S(t+1) is kept in the storage type, so every value is rounded exactly as in two single steps:
 // the result equals them bit for bit.  DRAM sees one read and one write of every population per
 // two steps, plus halo rows that neighbouring tiles (running at the same time) mostly take from L2.
-constexpr int kTbW = 128, kTbH = 32, kTbPrefetch = 2;
+constexpr int kTbW = 128, kTbPrefetch = 2;
 constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+131
 constexpr int kTbR0 = 4, kTbR1 = 3;        // ring depths in 4-row blocks
 
@@ -460,7 +461,8 @@ __device__ __forceinline__ void tb_pull4(const float *row, int lane, float (&out
 
 template <class S>
 __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__restrict__ src, float *__restrict__ dst,
-                                                              int nx, int ny, long long pitch, CollideCoef<float> cf) {
+                                                              int nx, int ny, long long pitch, int H,
+                                                              CollideCoef<float> cf) {
     static_assert(S::D == 2, "two-step tiles are 2D");
     constexpr int Q = S::Q;
     extern __shared__ __align__(16) float tb_smem[];
@@ -469,13 +471,13 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
     auto r0 = [&](int blk, int w, int i) { return ring0 + (((blk % kTbR0) * 4 + w) * Q + i) * kTbRow; };
     auto r1 = [&](int blk, int w, int i) { return ring1 + (((blk % kTbR1) * 4 + w) * Q + i) * kTbRow; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * kTbH;
-    const int iters = kTbH / 4 + 3;
+    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * H;
+    const int iters = H / 4 + 3;
 
     // Block k of S(t): row y0 - 2 + 4k + warp, chunks of 4 columns starting at x0 - 4 (periodic).
     auto load_block = [&](int k) {
         const int row = y0 - 2 + 4 * k + warp;
-        if (row <= y0 + kTbH + 1) {
+        if (row <= y0 + H + 1) {
             int r = row % ny;
             if (r < 0) r += ny;
             const long long rowoff = (long long)r * nx;
@@ -496,9 +498,9 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
         cp_async_wait<kTbPrefetch - 1>();
         __syncthreads();  // L_k complete and visible; A_{k-1} complete (read by B_k)
         load_block(k + kTbPrefetch);  // ring slot (k+2) % 4: neither L_{k-1} nor L_k
-        // ---- A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + kTbH are not needed)
+        // ---- A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + H are not needed)
         const int a = y0 + 4 * k - 5 + warp;
-        if (k >= 1 && a <= y0 + kTbH) {
+        if (k >= 1 && a <= y0 + H) {
             float pull[Q][4], post[Q][4];
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
         }
         // ---- B_k: S(t+2) row b = y0 + 4k - 12 + warp from A_{k-2}, A_{k-1}
         const int b = y0 + 4 * k - 12 + warp;
-        if (k >= 3 && b < y0 + kTbH) {
+        if (k >= 3 && b < y0 + H) {
             float pull[Q][4], post[Q][4];
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;

@@ -257,6 +257,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
         h->ghost_L = (int)(cfg->nx > cfg->ny ? cfg->nx : cfg->ny);
         e = cudaMalloc(&h->ghost, (cfg->storage == LEE_STORE_F64 ? 8 : 4) * 4 * (size_t)h->ghost_L);
     }
+    if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
+        e = o->step2_prepare();
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);

@@ -36,6 +36,8 @@ struct SetOps {
     // two fused steps per launch (periodic 2D FP32 grids with nx % 128 == 0; nullptr otherwise):
     // reads L.src, writes the state two steps later into L.dst
     cudaError_t (*step2)(const StepLaunch &);
+    // one-time set-up of the two-step kernel on the current device (outside stream capture)
+    cudaError_t (*step2_prepare)();
     // g = g^eq(fields) (fields FP64 on device)
     cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                         long long pitch, const SetConsts &k, cudaStream_t st);

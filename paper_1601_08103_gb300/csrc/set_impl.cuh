@@ -141,6 +141,32 @@ struct SetImpl {
             });
         }
     }
+    // Resident capacity of the two-step kernel (blocks per SM x SMs) per device, set by
+    // step2_prepare outside any stream capture.
+    static int *step2_capacity() {
+        static int cap[64] = {0};
+        return cap;
+    }
+    static cudaError_t step2_prepare() {
+        if constexpr (S::D != 2) {
+            return cudaErrorInvalidValue;
+        } else {
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e != cudaSuccess) return e;
+            if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+            if (step2_capacity()[dev]) return cudaSuccess;
+            constexpr int smem = tb_smem_bytes<S>();
+            e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step<S>, 128, smem);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            step2_capacity()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+            return cudaSuccess;
+        }
+    }
     static cudaError_t step2(const StepLaunch &L) {
         if constexpr (S::D != 2) {
             return cudaErrorInvalidValue;
@@ -148,11 +174,21 @@ struct SetImpl {
             if (L.storage != LEE_STORE_F32 || L.open || L.nx % kTbW != 0 || L.ny < 3) return cudaErrorInvalidValue;
             const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
             constexpr int smem = tb_smem_bytes<S>();
-            cudaError_t e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
             if (e != cudaSuccess) return e;
-            const dim3 grid(L.nx / kTbW, (L.ny + kTbH - 1) / kTbH);
+            if (dev < 0 || dev >= 64 || step2_capacity()[dev] == 0) return cudaErrorNotReady;  // prepare first
+            // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
+            const int strips = L.nx / kTbW;
+            int segs = step2_capacity()[dev] / strips;
+            if (segs < 1) segs = 1;
+            int H = (L.ny + segs - 1) / segs;
+            H = (H + 3) / 4 * 4;
+            if (H < 16) H = 16;
+            const dim3 grid(strips, (L.ny + H - 1) / H);
             k_stream_collide_2step<S><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
-                                                                     static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, cf);
+                                                                     static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, H,
+                                                                     cf);
             return cudaGetLastError();
         }
     }
@@ -170,6 +206,7 @@ struct SetImpl {
         o.sponge_damp = &sponge_damp;
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         o.step2 = S::D == 2 ? &step2 : nullptr;
+        o.step2_prepare = S::D == 2 ? &step2_prepare : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);
