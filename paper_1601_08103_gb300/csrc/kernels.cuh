@@ -498,17 +498,43 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
         cp_async_wait<kTbPrefetch - 1>();
         __syncthreads();  // L_k complete and visible; A_{k-1} complete (read by B_k)
         load_block(k + kTbPrefetch);  // ring slot (k+2) % 4: neither L_{k-1} nor L_k
-        // ---- A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + H are not needed)
+        // A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + H are not needed);
+        // B_k: S(t+2) row b = y0 + 4k - 12 + warp from A_{k-2}, A_{k-1}.  Both pulls are issued
+        // before either collision so that each warp has two independent streams of work.
         const int a = y0 + 4 * k - 5 + warp;
-        if (k >= 1 && a <= y0 + H) {
-            float pull[Q][4], post[Q][4];
+        const int b = y0 + 4 * k - 12 + warp;
+        const bool doA = k >= 1 && a <= y0 + H;  // warp-uniform
+        const bool doB = k >= 3 && b < y0 + H;
+        float pa[Q][4], pb[Q][4];
+        if (doB) {
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                const int rr = b - cy - (y0 - 5);  // row within the S(t+1) blocks
+                tb_pull4<cx>(r1(rr >> 2, rr & 3, i), lane, pb[i]);
+            });
+        }
+        if (doA) {
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
                 const int rr = a - cy - (y0 - 2);  // row within the S(t) blocks
-                tb_pull4<cx>(r0(rr >> 2, rr & 3, i), lane, pull[i]);
+                tb_pull4<cx>(r0(rr >> 2, rr & 3, i), lane, pa[i]);
             });
-            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pull, post, cf); });
+        }
+        if (doB) {
+            float post[Q][4];
+            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pb, post, cf); });
+            if (b < ny) {
+                float *outp = dst + (long long)b * nx + x0 + 4 * lane;
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    *reinterpret_cast<float4 *>(outp + (long long)i * pitch) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
+            }
+        }
+        if (doA) {
+            float post[Q][4];
+            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pa, post, cf); });
 #pragma unroll
             for (int i = 0; i < Q; ++i)
                 *reinterpret_cast<float4 *>(r1(k, warp, i) + 4 * lane + 4) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
@@ -525,24 +551,6 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
                 collide_cell<S, 0>(p1, q1, cf);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) r1(k, warp, i)[off] = q1[i][0];
-            }
-        }
-        // ---- B_k: S(t+2) row b = y0 + 4k - 12 + warp from A_{k-2}, A_{k-1}
-        const int b = y0 + 4 * k - 12 + warp;
-        if (k >= 3 && b < y0 + H) {
-            float pull[Q][4], post[Q][4];
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                const int rr = b - cy - (y0 - 5);  // row within the S(t+1) blocks
-                tb_pull4<cx>(r1(rr >> 2, rr & 3, i), lane, pull[i]);
-            });
-            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pull, post, cf); });
-            if (b < ny) {
-                float *outp = dst + (long long)b * nx + x0 + 4 * lane;
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    *reinterpret_cast<float4 *>(outp + (long long)i * pitch) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
             }
         }
     }
