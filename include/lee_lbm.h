@@ -126,7 +126,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  * n >= 8 the launches are replayed from a CUDA graph (one graph holding all n steps for
  * n <= 4096, else repeated 100-step graphs), captured on first use of that length on a private
  * stream and cached in the handle; results are identical to direct launches.  Periodic 2D FP32
- * grids with nx a multiple of 128 advance two steps per launch (lee_lbm_steps_per_launch).  A 1D
+ * grids with nx a multiple of 4 advance two steps per launch (lee_lbm_steps_per_launch).  A 1D
  * grid whose
  * two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB, e.g. D1Q3 FP64 up
  * to 4843 cells) runs all n >= 2 steps in one launch of a single-block kernel instead, again
@@ -168,7 +168,7 @@ lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t npa
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
 
 /* How lee_lbm_step runs this grid: *steps = 1 (one fused stream-collide launch per time step),
- * 2 (periodic 2D FP32 grids with nx a multiple of 128: two time steps per launch, the
+ * 2 (periodic 2D FP32 grids with nx a multiple of 4: two time steps per launch, the
  * intermediate state kept in shared memory -- temporal blocking) or 0 (small 1D grid: all steps
  * of a call in one on-chip launch).  All forms give bit-identical results. */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);

@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 }
 
 // ---------------------------------------------------------------------------------------------
-// two time steps per launch (temporal blocking) for periodic 2D FP32 grids
+// two time steps per launch (temporal blocking) for periodic 2D FP32 grids with nx % 4 == 0
 // ---------------------------------------------------------------------------------------------
 // A block (4 warps) owns an output tile of kTbW = 128 columns x H rows (H a multiple of 4, chosen
 // by the host so that all tiles are resident at once) and marches down it
@@ -482,9 +482,10 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
             if (r < 0) r += ny;
             const long long rowoff = (long long)r * nx;
             for (int c = lane; c < kTbRow / 4; c += 32) {
-                int x = x0 - 4 + 4 * c;
+                // periodic column (nx is a multiple of 4, so chunks stay 16-byte aligned); columns
+                // of the last strip past nx hold the periodic continuation of the row
+                int x = (x0 - 4 + 4 * c) % nx;
                 if (x < 0) x += nx;
-                if (x >= nx) x -= nx;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) cp_async_16(r0(k, warp, i) + 4 * c, src + (long long)i * pitch + rowoff + x);
             }
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
         if (doB) {
             float post[Q][4];
             static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pb, post, cf); });
-            if (b < ny) {
+            if (b < ny && x0 + 4 * lane < nx) {
                 float *outp = dst + (long long)b * nx + x0 + 4 * lane;
 #pragma unroll
                 for (int i = 0; i < Q; ++i)

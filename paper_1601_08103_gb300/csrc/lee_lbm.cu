@@ -360,9 +360,9 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         h->steps += n;
         return LEE_OK;
     }
-    // Periodic 2D FP32 grids whose width is a multiple of the tile: two steps per launch
+    // Periodic 2D FP32 grids whose width is a multiple of 4: two steps per launch
     // (temporal blocking; bit-identical to two single steps).
-    const bool two = h->ops->step2 && !L.open && h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 128 == 0 &&
+    const bool two = h->ops->step2 && !L.open && h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 4 == 0 &&
                      h->cfg.ny >= 3 && !h->single_step_only;
     const int unit = two ? 2 : 1;
     auto launch_unit = [&](int from, cudaStream_t st) -> cudaError_t {
@@ -526,7 +526,7 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
     const bool two = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
-                     h->cfg.nx % 128 == 0 && h->cfg.ny >= 3 && !h->single_step_only;
+                     h->cfg.nx % 4 == 0 && h->cfg.ny >= 3 && !h->single_step_only;
     const bool onchip = h->ops->onchip_1d && 2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
     *steps = onchip ? 0 : (two ? 2 : 1);
     return LEE_OK;

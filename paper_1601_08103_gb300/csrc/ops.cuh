@@ -33,7 +33,7 @@ struct SetOps {
     int D, Q;
     // one fused pull-stream + collide step
     cudaError_t (*step)(const StepLaunch &);
-    // two fused steps per launch (periodic 2D FP32 grids with nx % 128 == 0; nullptr otherwise):
+    // two fused steps per launch (periodic 2D FP32 grids with nx % 4 == 0; nullptr otherwise):
     // reads L.src, writes the state two steps later into L.dst
     cudaError_t (*step2)(const StepLaunch &);
     // one-time set-up of the two-step kernel on the current device (outside stream capture)

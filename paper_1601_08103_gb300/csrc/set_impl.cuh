@@ -171,7 +171,7 @@ struct SetImpl {
         if constexpr (S::D != 2) {
             return cudaErrorInvalidValue;
         } else {
-            if (L.storage != LEE_STORE_F32 || L.open || L.nx % kTbW != 0 || L.ny < 3) return cudaErrorInvalidValue;
+            if (L.storage != LEE_STORE_F32 || L.open || L.nx % 4 != 0 || L.ny < 3) return cudaErrorInvalidValue;
             const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
             constexpr int smem = tb_smem_bytes<S>();
             int dev = 0;
@@ -179,7 +179,7 @@ struct SetImpl {
             if (e != cudaSuccess) return e;
             if (dev < 0 || dev >= 64 || step2_capacity()[dev] == 0) return cudaErrorNotReady;  // prepare first
             // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
-            const int strips = L.nx / kTbW;
+            const int strips = (L.nx + kTbW - 1) / kTbW;
             int segs = step2_capacity()[dev] / strips;
             if (segs < 1) segs = 1;
             int H = (L.ny + segs - 1) / segs;

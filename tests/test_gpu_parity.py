@@ -258,6 +258,7 @@ def test_full_size_2d_config_against_oracle(gpu_lib):
                                                     ("D1Q3", (1000, 1, 1), "f16", "open_sponge"),
                                                     ("D2Q5", (260, 37, 1), "f32", "periodic"),
                                                     ("D2Q5", (256, 70, 1), "f32", "periodic"),
+                                                    ("D2Q5", (12, 5, 1), "f32", "periodic"),
                                                     ("D2Q5_DI", (128, 3, 1), "f32", "periodic"),
                                                     ("D3Q7", (36, 10, 7), "f16", "periodic"),
                                                     ("D2Q5", (64, 48, 1), "f64", "open_sponge"),
@@ -311,13 +312,13 @@ def test_1d_config_matches_oracle_and_dalembert(gpu_lib):
 
 @pytest.mark.parametrize("name", ["D2Q5", "D2Q5_DI"])
 def test_two_step_kernel_parity(gpu_lib, name):
-    """Periodic 2D FP32 grids with nx a multiple of 128 advance two steps per launch with the
-    intermediate state in shared memory; checked against the oracle on ragged tile rows."""
+    """Periodic 2D FP32 grids with nx a multiple of 4 advance two steps per launch with the
+    intermediate state in shared memory; checked against the oracle on full and partial
+    128-column strips, ragged tile rows and a grid narrower than one strip."""
     lee = gpu_lib
-    s = oracle.velset(name)
-    shape = (256, 37, 1)
-    for n, tau in ((2, 0.6), (3, 0.5), (50, 0.83)):
-        with lee.Solver(name, shape, tau, storage="f32") as sv:
-            assert sv.steps_per_launch == 2
-        r = run_pair(lee, name, shape, tau, n, storage="f32", seed=n + 40)
-        assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} two-step n={n}")
+    for shape in ((256, 37, 1), (260, 41, 1), (12, 5, 1)):
+        for n, tau in ((2, 0.6), (3, 0.5), (50, 0.83)):
+            with lee.Solver(name, shape, tau, storage="f32") as sv:
+                assert sv.steps_per_launch == 2
+            r = run_pair(lee, name, shape, tau, n, storage="f32", seed=n + 40)
+            assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} two-step {shape} n={n}")
