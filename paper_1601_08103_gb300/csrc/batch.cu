@@ -40,6 +40,29 @@ BatchedFn batched_fn(int V) {
     }
 }
 
+template <class S>
+cudaError_t launch_batched_2step(const void *src, void *dst, const void *doms, const unsigned short *table, int nblocks,
+                                 cudaStream_t st) {
+    k_stream_collide_2step_batched<S><<<nblocks, 128, tb_smem_bytes<S>(), st>>>(
+        static_cast<const float *>(src), static_cast<float *>(dst), static_cast<const TbDomain *>(doms), table);
+    return cudaGetLastError();
+}
+
+// Resident blocks of the batched two-step kernel on the current device (sets its shared-memory
+// attribute; called outside any stream capture).
+template <class S>
+cudaError_t prepare_batched_2step(int *capacity) {
+    constexpr int smem = tb_smem_bytes<S>();
+    cudaError_t e = cudaFuncSetAttribute(k_stream_collide_2step_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step_batched<S>, 128, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *capacity = per_sm * sms > 0 ? per_sm * sms : 1;
+    return e;
+}
+
 BatchedFn pick_batched(int set, int storage, int V) {
     if (set == LEE_D2Q5) return storage == LEE_STORE_F32 ? batched_fn<D2Q5, float>(V) : batched_fn<D2Q5, double>(V);
     if (set == LEE_D2Q5_DIATOMIC)
@@ -253,6 +276,58 @@ lee_status tune(lee_batch *b) {
     return LEE_OK;
 }
 
+// Two-step tiles: every tile covers about total_cells / capacity cells (128 columns x H rows),
+// so the whole batch is close to one resident wave of the two-step kernel.
+lee_status build_tb(lee_batch *b) {
+    int capacity = 1;
+    cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_2step<D2Q5>(&capacity) : prepare_batched_2step<D2Q5Di>(&capacity);
+    if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, std::string("two-step prepare: ") + cudaGetErrorString(e));
+    b->tb_fn = b->set == LEE_D2Q5 ? &launch_batched_2step<D2Q5> : &launch_batched_2step<D2Q5Di>;
+    const long long area = (b->total_cells + capacity - 1) / capacity;
+    std::vector<TbDomain> hd(b->count);
+    std::vector<unsigned short> table;
+    int block = 0;
+    for (int d = 0; d < b->count; ++d) {
+        TbDomain &D = hd[d];
+        D.nx = (int)b->doms[d].nx;
+        D.ny = (int)b->doms[d].ny;
+        long long H = (area + kTbW - 1) / kTbW;
+        H = (H + 3) / 4 * 4;
+        if (H < 16) H = 16;
+        const long long ny4 = ((long long)D.ny + 3) / 4 * 4;
+        if (H > ny4) H = ny4;
+        D.H = (int)H;
+        D.strips = (D.nx + kTbW - 1) / kTbW;
+        D.pitch = b->pitch[d];
+        D.offset = b->offset[d];
+        double M[4][4], N[4][4];
+        const double omega = omega_for(b->storage, b->doms[d].tau);
+        fold_coefficients(b->set, false, omega, M, N);
+        D.cf = make_coef<float>(omega, M, N);
+        D.first_block = block;
+        const int nb = D.strips * (int)((D.ny + H - 1) / H);
+        for (int k = 0; k < nb; ++k) table.push_back((unsigned short)d);
+        block += nb;
+    }
+    BCK(b, cudaMalloc(&b->d_tb, sizeof(TbDomain) * hd.size()), "cudaMalloc(two-step domains)");
+    BCK(b, cudaMalloc(&b->d_tb_table, sizeof(unsigned short) * table.size()), "cudaMalloc(two-step table)");
+    BCK(b, cudaMemcpyAsync(b->d_tb, hd.data(), sizeof(TbDomain) * hd.size(), cudaMemcpyHostToDevice, b->st), "H2D");
+    BCK(b, cudaMemcpyAsync(b->d_tb_table, table.data(), sizeof(unsigned short) * table.size(), cudaMemcpyHostToDevice,
+                           b->st),
+        "H2D");
+    BCK(b, cudaStreamSynchronize(b->st), "sync");
+    b->tb_blocks = block;
+    b->two = true;
+    return LEE_OK;
+}
+
+// One launch of the step unit (two fused steps when b->two, else one step) reading buffer
+// src_which and writing the other one.
+cudaError_t launch_unit(lee_batch *b, int src_which, cudaStream_t st) {
+    if (b->two) return b->tb_fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_tb, b->d_tb_table, b->tb_blocks, st);
+    return b->fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, st);
+}
+
 lee_status ensure_graph(lee_batch *b, int parity, long long steps, cudaGraphExec_t *out) {
     auto it = b->exec.find({parity, steps});
     if (it != b->exec.end()) {
@@ -262,8 +337,9 @@ lee_status ensure_graph(lee_batch *b, int parity, long long steps, cudaGraphExec
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     int w = parity;
-    for (long long k = 0; k < steps; ++k) {
-        cudaError_t e = b->fn(b->buf[w], b->buf[w ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, b->cap);
+    const int unit = b->two ? 2 : 1;
+    for (long long k = 0; k < steps / unit; ++k) {
+        cudaError_t e = launch_unit(b, w, b->cap);
         if (e != cudaSuccess) {
             cudaStreamEndCapture(b->cap, &g);
             if (g) cudaGraphDestroy(g);
@@ -348,6 +424,16 @@ lee_status lee_batch_create(int32_t set, int32_t storage, const lee_batch_domain
         cudaGetLastError();
         return s;
     }
+    bool two = storage == LEE_STORE_F32 && !(std::getenv("LEE_SINGLE_STEP") && std::getenv("LEE_SINGLE_STEP")[0] == '1');
+    for (int d = 0; d < count; ++d) two = two && domains[d].nx % 4 == 0 && domains[d].ny >= 3;
+    if (two) {
+        lee_status s2 = build_tb(b);
+        if (s2 != LEE_OK) {
+            lee_batch_destroy(b);
+            cudaGetLastError();
+            return s2;
+        }
+    }
     *out = b;
     return LEE_OK;
 }
@@ -402,19 +488,25 @@ lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode) {
         return LEE_OK;
     }
     if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
-    int64_t left = n;
+    const int unit = b->two ? 2 : 1;
+    int64_t units = n / unit;
     if (mode == LEE_BATCH_GRAPH) {
         // up to kMaxGraphSteps steps: one graph of all of them (one launch of the whole run);
-        // longer runs: replays of a kChunkSteps graph
-        const long long glen = left <= lee_batch::kMaxGraphSteps ? (left & ~1LL) : lee_batch::kChunkSteps;
-        while (glen > 0 && left >= glen) {
+        // longer runs: replays of a kChunkSteps graph.  Graphs hold an even number of launches.
+        const long long gunits = units * unit <= lee_batch::kMaxGraphSteps ? (units & ~1LL)
+                                                                           : (lee_batch::kChunkSteps / unit) & ~1LL;
+        while (gunits > 0 && units >= gunits) {
             cudaGraphExec_t ex = nullptr;
-            if ((s = ensure_graph(b, b->cur, glen, &ex)) != LEE_OK) return s;
-            BCK(b, cudaGraphLaunch(ex, b->st), "graph launch");  // even length: parity kept
-            left -= glen;
+            if ((s = ensure_graph(b, b->cur, gunits * unit, &ex)) != LEE_OK) return s;
+            BCK(b, cudaGraphLaunch(ex, b->st), "graph launch");  // even number of launches: parity kept
+            units -= gunits;
         }
     }
-    for (; left > 0; --left) {
+    for (; units > 0; --units) {
+        BCK(b, launch_unit(b, b->cur, b->st), "batched launch");
+        b->cur ^= 1;
+    }
+    for (int64_t left = n % unit; left > 0; --left) {
         if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
         b->cur ^= 1;
     }
@@ -529,6 +621,8 @@ lee_status lee_batch_destroy(lee_batch *b) {
     cudaFree(b->buf[1]);
     cudaFree(b->d_doms);
     cudaFree(b->d_table);
+    cudaFree(b->d_tb);
+    cudaFree(b->d_tb_table);
     cudaFree(b->fields);
     cudaFree(b->pops64);
     cudaFree(b->partial);

@@ -70,6 +70,12 @@ struct lee_batch {
     unsigned short *d_table = nullptr;
     size_t d_doms_cap = 0, d_table_cap = 0;
     lee::BatchedFn fn = nullptr;
+    // two fused steps per launch (FP32, every nx % 4 == 0): per-domain tiles and block table
+    bool two = false;
+    void *d_tb = nullptr;
+    unsigned short *d_tb_table = nullptr;
+    int tb_blocks = 0;
+    cudaError_t (*tb_fn)(const void *, void *, const void *, const unsigned short *, int, cudaStream_t) = nullptr;
     // captured graphs, keyed by (starting parity, number of steps); every graph has an even
     // number of steps, so replaying it leaves the buffer parity unchanged
     static constexpr int kMaxGraphSteps = 4096;

@@ -459,19 +459,18 @@ __device__ __forceinline__ void tb_pull4(const float *row, int lane, float (&out
     }
 }
 
+// One tile (columns x0 .. x0+127, rows y0 .. y0+H-1) of two fused steps; the whole block calls it.
 template <class S>
-__global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__restrict__ src, float *__restrict__ dst,
-                                                              int nx, int ny, long long pitch, int H,
-                                                              CollideCoef<float> cf) {
+__device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
+                                        long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
+                                        float *tb_smem) {
     static_assert(S::D == 2, "two-step tiles are 2D");
     constexpr int Q = S::Q;
-    extern __shared__ __align__(16) float tb_smem[];
     float *ring0 = tb_smem;                                // [kTbR0][4][Q][kTbRow]
     float *ring1 = tb_smem + kTbR0 * 4 * Q * kTbRow;       // [kTbR1][4][Q][kTbRow]
     auto r0 = [&](int blk, int w, int i) { return ring0 + (((blk % kTbR0) * 4 + w) * Q + i) * kTbRow; };
     auto r1 = [&](int blk, int w, int i) { return ring1 + (((blk % kTbR1) * 4 + w) * Q + i) * kTbRow; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * kTbW, y0 = blockIdx.y * H;
     const int iters = H / 4 + 3;
 
     // Block k of S(t): row y0 - 2 + 4k + warp, chunks of 4 columns starting at x0 - 4 (periodic).
@@ -556,6 +555,34 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
         }
     }
     cp_async_wait<0>();
+}
+
+template <class S>
+__global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__restrict__ src, float *__restrict__ dst,
+                                                              int nx, int ny, long long pitch, int H,
+                                                              CollideCoef<float> cf) {
+    extern __shared__ __align__(16) float tb_smem[];
+    tb_tile<S>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
+}
+
+// Two fused steps over many periodic domains: domain d owns blocks [first_block, first_block +
+// strips * segs); block lb of it is strip lb % strips, segment lb / strips.
+struct TbDomain {
+    int nx, ny, H, strips, first_block;
+    long long pitch, offset;
+    CollideCoef<float> cf;
+};
+
+template <class S>
+__global__ void __launch_bounds__(128) k_stream_collide_2step_batched(const float *__restrict__ src,
+                                                                      float *__restrict__ dst,
+                                                                      const TbDomain *__restrict__ doms,
+                                                                      const unsigned short *__restrict__ block_domain) {
+    extern __shared__ __align__(16) float tb_smem[];
+    const TbDomain &D = doms[block_domain[blockIdx.x]];
+    const int lb = blockIdx.x - D.first_block;
+    tb_tile<S>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, (lb % D.strips) * kTbW,
+               (lb / D.strips) * D.H, tb_smem);
 }
 
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
