@@ -49,8 +49,8 @@ lee_status lee_batch_init_fields(lee_batch *b, int32_t d, const double *rho, con
  * mode a run of up to 4096 steps is one launch of a graph holding all its steps (captured on
  * first use of that length and parity, then cached); longer runs replay a 100-step graph.  With
  * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance two steps per
- * launch (the intermediate state kept in shared memory; tiles of about total cells / resident
- * blocks each), bit-identical to single steps. */
+ * launch (the intermediate state kept in shared memory; tiles of 128 columns x up to 128 rows,
+ * dispatched largest first), bit-identical to single steps. */
 lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode);
 
 /* Per-cell moments of domain d (as lee_lbm_moments).  NULL outputs are skipped. */

@@ -41,10 +41,11 @@ BatchedFn batched_fn(int V) {
 }
 
 template <class S>
-cudaError_t launch_batched_2step(const void *src, void *dst, const void *doms, const unsigned short *table, int nblocks,
+cudaError_t launch_batched_2step(const void *src, void *dst, const void *doms, const void *tiles, int nblocks,
                                  cudaStream_t st) {
     k_stream_collide_2step_batched<S><<<nblocks, 128, tb_smem_bytes<S>(), st>>>(
-        static_cast<const float *>(src), static_cast<float *>(dst), static_cast<const TbDomain *>(doms), table);
+        static_cast<const float *>(src), static_cast<float *>(dst), static_cast<const TbDomain *>(doms),
+        static_cast<const int3 *>(tiles));
     return cudaGetLastError();
 }
 
@@ -276,47 +277,47 @@ lee_status tune(lee_batch *b) {
     return LEE_OK;
 }
 
-// Two-step tiles: every tile covers about total_cells / capacity cells (128 columns x H rows),
-// so the whole batch is close to one resident wave of the two-step kernel.
+// Two-step tiles of 128 columns x at most kBatchTileRows rows (fewer for short domains), listed
+// largest first so that the block scheduler balances the uneven domains.
+constexpr int kBatchTileRows = 128;
+
 lee_status build_tb(lee_batch *b) {
     int capacity = 1;
     cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_2step<D2Q5>(&capacity) : prepare_batched_2step<D2Q5Di>(&capacity);
     if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, std::string("two-step prepare: ") + cudaGetErrorString(e));
     b->tb_fn = b->set == LEE_D2Q5 ? &launch_batched_2step<D2Q5> : &launch_batched_2step<D2Q5Di>;
-    const long long area = (b->total_cells + capacity - 1) / capacity;
     std::vector<TbDomain> hd(b->count);
-    std::vector<unsigned short> table;
-    int block = 0;
+    struct Tile {
+        int rows, d, x0, y0;
+    };
+    std::vector<Tile> tiles;
     for (int d = 0; d < b->count; ++d) {
         TbDomain &D = hd[d];
         D.nx = (int)b->doms[d].nx;
         D.ny = (int)b->doms[d].ny;
-        long long H = (area + kTbW - 1) / kTbW;
-        H = (H + 3) / 4 * 4;
-        if (H < 16) H = 16;
-        const long long ny4 = ((long long)D.ny + 3) / 4 * 4;
+        int H = kBatchTileRows;
+        const int ny4 = (D.ny + 3) / 4 * 4;
         if (H > ny4) H = ny4;
-        D.H = (int)H;
-        D.strips = (D.nx + kTbW - 1) / kTbW;
+        D.H = H;
         D.pitch = b->pitch[d];
         D.offset = b->offset[d];
         double M[4][4], N[4][4];
         const double omega = omega_for(b->storage, b->doms[d].tau);
         fold_coefficients(b->set, false, omega, M, N);
         D.cf = make_coef<float>(omega, M, N);
-        D.first_block = block;
-        const int nb = D.strips * (int)((D.ny + H - 1) / H);
-        for (int k = 0; k < nb; ++k) table.push_back((unsigned short)d);
-        block += nb;
+        for (int y0 = 0; y0 < D.ny; y0 += H)
+            for (int x0 = 0; x0 < D.nx; x0 += kTbW) tiles.push_back({std::min(H, D.ny - y0), d, x0, y0});
     }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &p, const Tile &q) { return p.rows > q.rows; });
+    std::vector<int3> ht(tiles.size());
+    for (size_t k = 0; k < tiles.size(); ++k) ht[k] = make_int3(tiles[k].d, tiles[k].x0, tiles[k].y0);
     BCK(b, cudaMalloc(&b->d_tb, sizeof(TbDomain) * hd.size()), "cudaMalloc(two-step domains)");
-    BCK(b, cudaMalloc(&b->d_tb_table, sizeof(unsigned short) * table.size()), "cudaMalloc(two-step table)");
+    BCK(b, cudaMalloc(&b->d_tb_tiles, sizeof(int3) * ht.size()), "cudaMalloc(two-step tiles)");
     BCK(b, cudaMemcpyAsync(b->d_tb, hd.data(), sizeof(TbDomain) * hd.size(), cudaMemcpyHostToDevice, b->st), "H2D");
-    BCK(b, cudaMemcpyAsync(b->d_tb_table, table.data(), sizeof(unsigned short) * table.size(), cudaMemcpyHostToDevice,
-                           b->st),
-        "H2D");
+    BCK(b, cudaMemcpyAsync(b->d_tb_tiles, ht.data(), sizeof(int3) * ht.size(), cudaMemcpyHostToDevice, b->st), "H2D");
     BCK(b, cudaStreamSynchronize(b->st), "sync");
-    b->tb_blocks = block;
+    (void)capacity;
+    b->tb_blocks = (int)ht.size();
     b->two = true;
     return LEE_OK;
 }
@@ -324,7 +325,7 @@ lee_status build_tb(lee_batch *b) {
 // One launch of the step unit (two fused steps when b->two, else one step) reading buffer
 // src_which and writing the other one.
 cudaError_t launch_unit(lee_batch *b, int src_which, cudaStream_t st) {
-    if (b->two) return b->tb_fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_tb, b->d_tb_table, b->tb_blocks, st);
+    if (b->two) return b->tb_fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_tb, b->d_tb_tiles, b->tb_blocks, st);
     return b->fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, st);
 }
 
@@ -622,7 +623,7 @@ lee_status lee_batch_destroy(lee_batch *b) {
     cudaFree(b->d_doms);
     cudaFree(b->d_table);
     cudaFree(b->d_tb);
-    cudaFree(b->d_tb_table);
+    cudaFree(b->d_tb_tiles);
     cudaFree(b->fields);
     cudaFree(b->pops64);
     cudaFree(b->partial);

@@ -73,9 +73,9 @@ struct lee_batch {
     // two fused steps per launch (FP32, every nx % 4 == 0): per-domain tiles and block table
     bool two = false;
     void *d_tb = nullptr;
-    unsigned short *d_tb_table = nullptr;
+    void *d_tb_tiles = nullptr;  // int3 (domain, x0, y0) per block, largest tiles first
     int tb_blocks = 0;
-    cudaError_t (*tb_fn)(const void *, void *, const void *, const unsigned short *, int, cudaStream_t) = nullptr;
+    cudaError_t (*tb_fn)(const void *, void *, const void *, const void *, int, cudaStream_t) = nullptr;
     // captured graphs, keyed by (starting parity, number of steps); every graph has an even
     // number of steps, so replaying it leaves the buffer parity unchanged
     static constexpr int kMaxGraphSteps = 4096;

@@ -565,10 +565,11 @@ __global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__res
     tb_tile<S>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
 }
 
-// Two fused steps over many periodic domains: domain d owns blocks [first_block, first_block +
-// strips * segs); block lb of it is strip lb % strips, segment lb / strips.
+// Two fused steps over many periodic domains.  Block b works on tile tiles[b] = (domain,
+// x0, y0) of height doms[domain].H; the host orders the tiles largest first so that the block
+// scheduler balances uneven domains.
 struct TbDomain {
-    int nx, ny, H, strips, first_block;
+    int nx, ny, H;
     long long pitch, offset;
     CollideCoef<float> cf;
 };
@@ -577,12 +578,11 @@ template <class S>
 __global__ void __launch_bounds__(128) k_stream_collide_2step_batched(const float *__restrict__ src,
                                                                       float *__restrict__ dst,
                                                                       const TbDomain *__restrict__ doms,
-                                                                      const unsigned short *__restrict__ block_domain) {
+                                                                      const int3 *__restrict__ tiles) {
     extern __shared__ __align__(16) float tb_smem[];
-    const TbDomain &D = doms[block_domain[blockIdx.x]];
-    const int lb = blockIdx.x - D.first_block;
-    tb_tile<S>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, (lb % D.strips) * kTbW,
-               (lb / D.strips) * D.H, tb_smem);
+    const int3 tl = tiles[blockIdx.x];
+    const TbDomain &D = doms[tl.x];
+    tb_tile<S>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
 }
 
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
