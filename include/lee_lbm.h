@@ -109,6 +109,28 @@ const char *lee_status_string(lee_status s);
  * Returns LEE_ERR_INVALID_ARGUMENT for an unknown set or NULL D/q. */
 lee_status lee_velset_info(int32_t set, int32_t *D, int32_t *q, int32_t *c, double *f, double *beta, double *consts);
 
+/* Scales between a dimensional problem and the lattice (Sec. 2.1 non-dimensionalisation, Sec. 6
+ * lattice with dx = dt).  A dimensional quantity is its scale times the non-dimensional one:
+ * rho0_dim = rho_star rho0, theta0_dim = theta_star theta0, u_dim = u_star u, x_dim = x_star x,
+ * t_dim = t_star t, with u_star = x_star / t_star and u_star^2 = theta_star; the velocity set
+ * fixes the non-dimensional rho0, theta0 (Sec. 8). */
+typedef struct {
+    double rho_star, theta_star, u_star, x_star, t_star;
+    double eps;       /* lattice spacing = time step, (length_dim / x_star) / n_cells */
+    double t_end;     /* non-dimensional end time, t_end_dim / t_star */
+    int64_t steps;    /* N_TS = round(t_end / eps), halves rounded away from zero */
+    double mismatch;  /* t_end - steps * eps: the end-time error of the lattice run (Sec. 9, Table 1) */
+} lee_units;
+
+/* Fills *out for velocity set `set`, a dimensional background rho0_dim, theta0_dim (> 0), a length
+ * scale x_star (> 0), a periodic domain of dimensional length length_dim (> 0) resolved by n_cells
+ * (>= 1) cells per direction, and a dimensional end time t_end_dim (>= 0).  Host-only, no device
+ * needed.  Initial fields convert as rho' = rho'_dim / rho_star, u' = u'_dim / u_star,
+ * theta' = theta'_dim / theta_star.  LEE_ERR_INVALID_ARGUMENT for an unknown set, a NULL out, a
+ * non-finite or out-of-range argument, or a step count beyond 2^62. */
+lee_status lee_units_from_dimensional(int32_t set, double rho0_dim, double theta0_dim, double x_star,
+                                      double length_dim, int64_t n_cells, double t_end_dim, lee_units *out);
+
 /* Creates a solver for cfg on the current CUDA device.  Validates the configuration (tau >= 1/2,
  * extents >= 1 and consistent with the dimension, storage/bc/set combination), allocates the
  * ping-pong population buffers, field staging and reduction scratch on the device, and leaves the

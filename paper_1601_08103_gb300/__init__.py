@@ -50,6 +50,12 @@ class lee_lbm_config(ctypes.Structure):
                 ("store_scale", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
 
 
+class lee_units(ctypes.Structure):
+    _fields_ = [("rho_star", ctypes.c_double), ("theta_star", ctypes.c_double), ("u_star", ctypes.c_double),
+                ("x_star", ctypes.c_double), ("t_star", ctypes.c_double), ("eps", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("steps", ctypes.c_int64), ("mismatch", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -58,6 +64,7 @@ _I32, _I64, _D, _P = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_v
 _SIGS = {
     "lee_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lee_velset_info": (ctypes.c_int, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P, _P, _P, _P]),
+    "lee_units_from_dimensional": (ctypes.c_int, [_I32, _D, _D, _D, _D, _I64, _D, ctypes.POINTER(lee_units)]),
     "lee_lbm_create": (ctypes.c_int, [ctypes.POINTER(lee_lbm_config), ctypes.POINTER(_P)]),
     "lee_lbm_init_fields": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
     "lee_lbm_step": (ctypes.c_int, [_P, _I64]),
@@ -171,6 +178,18 @@ def lee_velset_info(set_name: str) -> dict:
            "f": [f[i] for i in range(n)], "beta": [beta[i] for i in range(n)]}
     out.update({k: consts[j] for j, k in enumerate(keys)})
     return out
+
+
+def lee_units_from_dimensional(set_name: str, rho0_dim: float, theta0_dim: float, x_star: float, length_dim: float,
+                               n_cells: int, t_end_dim: float) -> dict:
+    """Scales of a dimensional problem on the lattice (Sec. 2.1, Sec. 6): rho_star, theta_star,
+    u_star, x_star, t_star, the lattice step eps, the non-dimensional end time t_end, the step
+    count steps = round(t_end / eps) and the end-time mismatch t_end - steps * eps."""
+    u = lee_units()
+    _check(load().lee_units_from_dimensional(SETS[set_name], float(rho0_dim), float(theta0_dim), float(x_star),
+                                             float(length_dim), int(n_cells), float(t_end_dim), ctypes.byref(u)),
+           "lee_units_from_dimensional")
+    return {name: getattr(u, name) for name, _ in lee_units._fields_}
 
 
 def make_config(set_name: str, shape, tau: float, storage: str = "f64", bc: str = "periodic", sponge_width: int = 0,

@@ -200,6 +200,30 @@ lee_status lee_velset_info(int32_t set, int32_t *D, int32_t *q, int32_t *c, doub
     return LEE_OK;
 }
 
+lee_status lee_units_from_dimensional(int32_t set, double rho0_dim, double theta0_dim, double x_star,
+                                      double length_dim, int64_t n_cells, double t_end_dim, lee_units *out) {
+    if (!out || !set_ops(set)) return LEE_ERR_INVALID_ARGUMENT;
+    const double pos[4] = {rho0_dim, theta0_dim, x_star, length_dim};
+    for (double v : pos)
+        if (!std::isfinite(v) || !(v > 0.0)) return LEE_ERR_INVALID_ARGUMENT;
+    if (n_cells < 1 || !std::isfinite(t_end_dim) || !(t_end_dim >= 0.0)) return LEE_ERR_INVALID_ARGUMENT;
+    const SetConsts k = consts_for(set, 1.0);
+    lee_units u;
+    u.rho_star = rho0_dim / k.rho0;
+    u.theta_star = theta0_dim / k.theta0;
+    u.u_star = std::sqrt(u.theta_star);
+    u.x_star = x_star;
+    u.t_star = x_star / u.u_star;
+    u.eps = (length_dim / x_star) / (double)n_cells;
+    u.t_end = t_end_dim / u.t_star;
+    const double r = std::round(u.t_end / u.eps);
+    if (!std::isfinite(r) || r > 4.6e18) return LEE_ERR_INVALID_ARGUMENT;
+    u.steps = (int64_t)r;
+    u.mismatch = u.t_end - (double)u.steps * u.eps;
+    *out = u;
+    return LEE_OK;
+}
+
 lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (!out) return LEE_ERR_INVALID_ARGUMENT;
     *out = nullptr;

@@ -11,6 +11,8 @@ Tolerances (relative L2 over all compared values, plus an element-wise max check
   16-bit:       measured storage error, bounded loosely by u * sqrt(10 n) * 4 (u = 2^-11 FP16,
                 2^-8 BF16).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -322,3 +324,22 @@ def test_two_step_kernel_parity(gpu_lib, name):
                 assert sv.steps_per_launch == 2
             r = run_pair(lee, name, shape, tau, n, storage="f32", seed=n + 40)
             assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} two-step {shape} n={n}")
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_3d_diatomic_pulse_in_dimensional_units(gpu_lib, storage):
+    """The 3D diatomic run of Sec. 9.3 set up from its dimensional data: background density and
+    temperature 1, domain [0, 2)^3 with N = 40 cells per direction, end time 1, density pulse
+    exp(-15 |x - (1,1,1)|^2).  The library's units give N_TS = round(sqrt(21/5) / dt) = 41 steps;
+    the run (tau = 1/2) is compared with the oracle."""
+    lee = gpu_lib
+    name, n = "D3Q7_DI", 40
+    un = lee.lee_units_from_dimensional(name, 1.0, 1.0, 1.0, 2.0, n, 1.0)
+    assert un["steps"] == 41
+    eps = un["eps"]
+    shape = (n, n, n)
+    rho = inputs.gaussian_pulse(shape, 1.0 / un["rho_star"], 1.0 / (math.sqrt(15.0) * eps), (n / 2, n / 2, n / 2))
+    u, th = inputs.zero_rest(3, n ** 3)
+    r = run_pair(lee, name, shape, 0.5, un["steps"], storage=storage, fields=(rho, u, th))
+    assert_close(r["g_gpu"], r["g_ora"], TOL[storage], f"{name} {storage} dimensional pulse")
+    assert_close(r["m_gpu"][0], r["m_ora"][0], TOL[storage], "rho'")
