@@ -46,6 +46,9 @@ struct lee_lbm {
     // set by LEE_SINGLE_STEP=1 in the environment at create time: never fuse two steps per
     // launch (for comparisons against the one-step kernel)
     bool single_step_only = false;
+    // set by LEE_FORCE_SCALAR=1 at create time: one cell per thread in every step kernel, and one
+    // step per launch (for comparisons of the vector and packed paths against the scalar one)
+    bool force_scalar = false;
 };
 
 namespace lee {

@@ -165,6 +165,36 @@ struct OpenEdge {
 // ---------------------------------------------------------------------------------------------
 // collision of one cell (index K of the per-thread vector)
 // ---------------------------------------------------------------------------------------------
+template <class S>
+__host__ __device__ constexpr int first_in_shell(int s) {
+    for (int i = 0; i < S::Q; ++i)
+        if (S::shell(i) == s) return i;
+    return -1;
+}
+template <class S>
+__host__ __device__ constexpr int first_on_axis(int s, int a) {
+    for (int i = 0; i < S::Q; ++i)
+        if (S::shell(i) == s && S::c(i, a) != 0) return i;
+    return -1;
+}
+template <class S>
+__host__ __device__ constexpr int first_present_shell(int from) {
+    for (int s = from; s < 4; ++s)
+        if (shell_present<S>(s)) return s;
+    return -1;
+}
+
+template <class S>
+__host__ __device__ constexpr int moving_shells() {
+    int n = 0;
+    for (int s = 1; s < 4; ++s) n += shell_present<S>(s) ? 1 : 0;
+    return n;
+}
+
+// Every rounding is spelled out so that no result depends on the compiler's contraction of a
+// multiply and an add: with one moving shell the momentum term of velocity i is one fused
+// multiply-add per axis, eq = fma(+-N[t][s1], J[s1][a], eq); with several moving shells the sums
+// KJ[t][a] = sum_s N[t][s] J[s][a] (a chain of fused multiply-adds) are added to eq.
 template <class S, int K, class C, int V>
 __device__ __forceinline__ void collide_cell(const C (&g)[S::Q][V], C (&out)[S::Q][V], const CollideCoef<C> &cf) {
     // Accumulators start at -0.0 so that the first addition folds away exactly.
@@ -199,7 +229,7 @@ __device__ __forceinline__ void collide_cell(const C (&g)[S::Q][V], C (&out)[S::
                 if constexpr (shell_present<S>(s)) acc = fma(cf.M[t][s], P[s], acc);
             });
             B[t] = acc;
-            if constexpr (t > 0) {
+            if constexpr (t > 0 && moving_shells<S>() > 1) {
                 static_for<S::D>([&](auto A) {
                     constexpr int a = decltype(A)::value;
                     C kj = C(-0.0);
@@ -218,11 +248,116 @@ __device__ __forceinline__ void collide_cell(const C (&g)[S::Q][V], C (&out)[S::
         C eq = B[t];
         static_for<S::D>([&](auto A) {
             constexpr int a = decltype(A)::value;
-            if constexpr (S::c(i, a) == 1) eq += KJ[t][a];
-            if constexpr (S::c(i, a) == -1) eq -= KJ[t][a];
+            constexpr int c = S::c(i, a);
+            if constexpr (c != 0 && moving_shells<S>() == 1) {
+                constexpr int s1 = first_present_shell<S>(1);
+                eq = fma(c == 1 ? cf.N[t][s1] : -cf.N[t][s1], J[s1][a], eq);
+            } else if constexpr (c == 1) {
+                eq += KJ[t][a];
+            } else if constexpr (c == -1) {
+                eq -= KJ[t][a];
+            }
         });
         out[i][K] = fma(cf.one_minus_omega, g[i][K], eq);
     });
+}
+
+// FP32 collision of two cells (K, K+1) at once with the packed f32x2 add, mul and fma of sm_100
+// and later.  Every packed operation rounds each half exactly like the scalar operation it
+// replaces in collide_cell (a - b is a + (-b); a first accumulation into -0.0 is the value itself,
+// or a plain product for the fma chains), so the result is the same bit for bit with half the FP
+// instructions.
+__device__ __forceinline__ float2 splat2(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+template <class S, int K, int V>
+__device__ __forceinline__ void collide_pair(const float (&g)[S::Q][V], float (&out)[S::Q][V],
+                                             const CollideCoef<float> &cf) {
+    static_assert(K + 1 < V, "a pair needs two cells");
+    float2 P[4], J[4][3];
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int s = S::shell(i);
+        const float2 v = make_float2(g[i][K], g[i][K + 1]);
+        if constexpr (i == first_in_shell<S>(s)) P[s] = v;
+        else P[s] = __fadd2_rn(P[s], v);
+        static_for<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            constexpr int c = S::c(i, a);
+            if constexpr (c != 0) {
+                const float2 sv = c == 1 ? v : neg2(v);
+                if constexpr (i == first_on_axis<S>(s, a)) J[s][a] = sv;
+                else J[s][a] = __fadd2_rn(J[s][a], sv);
+            }
+        });
+    });
+    float2 B[4], KJ[4][3];
+    static_for<4>([&](auto T) {
+        constexpr int t = decltype(T)::value;
+        if constexpr (shell_present<S>(t)) {
+            constexpr int s0 = first_present_shell<S>(0);
+            float2 acc;
+            static_for<4>([&](auto Sx) {
+                constexpr int s = decltype(Sx)::value;
+                if constexpr (shell_present<S>(s)) {
+                    if constexpr (s == s0) acc = __fmul2_rn(splat2(cf.Mlo[t][s]), P[s]);
+                    else acc = __ffma2_rn(splat2(cf.Mlo[t][s]), P[s], acc);
+                }
+            });
+            static_for<4>([&](auto Sx) {
+                constexpr int s = decltype(Sx)::value;
+                if constexpr (shell_present<S>(s)) acc = __ffma2_rn(splat2(cf.M[t][s]), P[s], acc);
+            });
+            B[t] = acc;
+            if constexpr (t > 0 && moving_shells<S>() > 1) {
+                constexpr int s1 = first_present_shell<S>(1);
+                static_for<S::D>([&](auto A) {
+                    constexpr int a = decltype(A)::value;
+                    float2 kj;
+                    static_for<4>([&](auto Sx) {
+                        constexpr int s = decltype(Sx)::value;
+                        if constexpr (s > 0 && shell_present<S>(s)) {
+                            if constexpr (s == s1) kj = __fmul2_rn(splat2(cf.N[t][s]), J[s][a]);
+                            else kj = __ffma2_rn(splat2(cf.N[t][s]), J[s][a], kj);
+                        }
+                    });
+                    KJ[t][a] = kj;
+                });
+            }
+        }
+    });
+    const float2 omm = splat2(cf.one_minus_omega);
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int t = S::shell(i);
+        float2 eq = B[t];
+        static_for<S::D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            constexpr int c = S::c(i, a);
+            if constexpr (c != 0 && moving_shells<S>() == 1) {
+                constexpr int s1 = first_present_shell<S>(1);
+                eq = __ffma2_rn(splat2(c == 1 ? cf.N[t][s1] : -cf.N[t][s1]), J[s1][a], eq);
+            } else if constexpr (c == 1) {
+                eq = __fadd2_rn(eq, KJ[t][a]);
+            } else if constexpr (c == -1) {
+                eq = __fadd2_rn(eq, neg2(KJ[t][a]));
+            }
+        });
+        const float2 r = __ffma2_rn(omm, make_float2(g[i][K], g[i][K + 1]), eq);
+        out[i][K] = r.x;
+        out[i][K + 1] = r.y;
+    });
+}
+
+// All V cells of a chunk: FP32 pairs on the packed path, anything else one cell at a time (both
+// give the same bits).
+template <class S, bool PACK = true, class C, int V>
+__device__ __forceinline__ void collide_chunk(const C (&g)[S::Q][V], C (&out)[S::Q][V], const CollideCoef<C> &cf) {
+    if constexpr (PACK && std::is_same<C, float>::value && V % 2 == 0) {
+        static_for<V / 2>([&](auto Kx) { collide_pair<S, 2 * decltype(Kx)::value>(g, out, cf); });
+    } else {
+        static_for<V>([&](auto Kx) { collide_cell<S, decltype(Kx)::value>(g, out, cf); });
+    }
 }
 
 template <class C>
@@ -239,7 +374,7 @@ __device__ __forceinline__ C sponge_factor(int x, int y, int z, const GridDesc &
     }
     if (d <= 0) return C(1);
     const C r = C(d) / C(w);
-    return C(1) - smax * r * r;
+    return fma(-(smax * r), r, C(1));  // 1 - smax r^2, one rounding of the product (smax r) r
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -334,7 +469,7 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
     });
 
     C post[S::Q][V];
-    static_for<V>([&](auto Kx) { collide_cell<S, decltype(Kx)::value>(pull, post, cf); });
+    collide_chunk<S>(pull, post, cf);
 
     if constexpr (OPEN) {
         if (ob.sponge_w > 0) {
@@ -410,22 +545,29 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 // ---------------------------------------------------------------------------------------------
 // two time steps per launch (temporal blocking) for periodic 2D FP32 grids with nx % 4 == 0
 // ---------------------------------------------------------------------------------------------
-// A block (4 warps) owns an output tile of kTbW = 128 columns x H rows (H a multiple of 4, chosen
-// by the host so that all tiles are resident at once) and marches down it
-// four rows per iteration, one row per warp, four cells (one float4) per lane.  Output row b at
-// t+2 needs S(t+1) on rows b-1..b+1 and columns x0-1..x0+128, which needs S(t) on rows b-2..b+2
-// and columns x0-2..x0+129.  Per iteration k (row blocks of 4):
+// A block (4 warps) owns an output tile of kTbW columns x H rows (H a multiple of 4, chosen by
+// the host so that all tiles are resident at once) and marches down it four rows per iteration,
+// one row per warp, kTbV = kTbW / 32 cells per lane.  Output row b at t+2 needs S(t+1) on rows
+// b-1..b+1 and columns x0-1..x0+kTbW, which needs S(t) on rows b-2..b+2 and columns
+// x0-2..x0+kTbW+1.  Per iteration k (row blocks of 4):
 //   L_k: S(t) rows y0-2+4k .. y0+1+4k stream in by 16-byte cp.async, kTbPrefetch blocks ahead,
-//        into a 4-block ring (columns x0-4 .. x0+131, so every chunk is 16-byte aligned);
+//        into a 4-block ring (columns x0-4 .. x0+kTbW+3, so every chunk is 16-byte aligned);
 //   A_k: S(t+1) rows y0+4k-5 .. y0+4k-2 from L_{k-1}, L_k into a 3-block ring;
 //   B_k: S(t+2) rows y0+4k-12 .. y0+4k-9 from A_{k-2}, A_{k-1}, stored to global memory.
 // B_k does not read A_k, so one barrier per iteration separates all producers and consumers.
 // S(t+1) is kept in the storage type, so every value is rounded exactly as in two single steps:
 // the result equals them bit for bit.  DRAM sees one read and one write of every population per
 // two steps, plus halo rows that neighbouring tiles (running at the same time) mostly take from L2.
+// The rings take (4 + 3) * 4 * q * (kTbW + 8) floats of shared memory per block, which sets how
+// many blocks (and warps) an SM holds: 76 KB and 3 blocks for D2Q5 at kTbW = 128, 40 KB and 5
+// blocks at kTbW = 64.
 constexpr int kTbW = 128, kTbPrefetch = 2;
-constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+131
+constexpr int kTbV = kTbW / 32;            // cells per lane
+constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+kTbW+3
+constexpr int kTbChunks = kTbRow / 4;      // 16-byte chunks per ring row
 constexpr int kTbR0 = 4, kTbR1 = 3;        // ring depths in 4-row blocks
+constexpr bool kTbPacked = true;           // collide a lane's cells as f32x2 pairs
+static_assert(kTbW == 64 || kTbW == 128, "two or four cells per lane");
 
 template <class S>
 constexpr int tb_smem_bytes() {
@@ -440,26 +582,48 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Pulls the four cells of one lane for velocity i from a ring row (offsets relative to x0-4):
-// the lane's own float4 sits at 4*lane+4; c_x = +1 takes one element from the left neighbour
-// lane (or offset 3 for lane 0), c_x = -1 one from the right neighbour (or offset 132 for lane 31).
-template <int cx>
-__device__ __forceinline__ void tb_pull4(const float *row, int lane, float (&out)[4]) {
-    const float4 v = *reinterpret_cast<const float4 *>(row + 4 * lane + 4);
-    if constexpr (cx == 0) {
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
-    } else if constexpr (cx == 1) {
-        float left = __shfl_up_sync(kFull, v.w, 1);
-        if (lane == 0) left = row[3];
-        out[0] = left; out[1] = v.x; out[2] = v.y; out[3] = v.z;
+// kTbV consecutive floats of a ring row (aligned to kTbV floats) and their store.
+__device__ __forceinline__ void tb_ld(const float *p, float (&v)[kTbV]) {
+    if constexpr (kTbV == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     } else {
-        float right = __shfl_down_sync(kFull, v.x, 1);
-        if (lane == 31) right = row[132];
-        out[0] = v.y; out[1] = v.z; out[2] = v.w; out[3] = right;
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+__device__ __forceinline__ void tb_st(float *p, const float (&v)[kTbV]) {
+    if constexpr (kTbV == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// Pulls the kTbV cells of one lane for velocity i from a ring row (offsets relative to x0-4):
+// the lane's own cells sit at kTbV*lane+4; c_x = +1 takes one element from the left neighbour
+// lane (or offset 3 for lane 0), c_x = -1 one from the right neighbour (or offset kTbW+4 for
+// lane 31).
+template <int cx>
+__device__ __forceinline__ void tb_pull(const float *row, int lane, float (&out)[kTbV]) {
+    float v[kTbV];
+    tb_ld(row + kTbV * lane + 4, v);
+    if constexpr (cx == 0) {
+#pragma unroll
+        for (int e = 0; e < kTbV; ++e) out[e] = v[e];
+    } else if constexpr (cx == 1) {
+        float left = __shfl_up_sync(kFull, v[kTbV - 1], 1);
+        if (lane == 0) left = row[3];
+        out[0] = left;
+#pragma unroll
+        for (int e = 1; e < kTbV; ++e) out[e] = v[e - 1];
+    } else {
+        float right = __shfl_down_sync(kFull, v[0], 1);
+        if (lane == 31) right = row[kTbW + 4];
+#pragma unroll
+        for (int e = 0; e + 1 < kTbV; ++e) out[e] = v[e + 1];
+        out[kTbV - 1] = right;
     }
 }
 
-// One tile (columns x0 .. x0+127, rows y0 .. y0+H-1) of two fused steps; the whole block calls it.
+// One tile (columns x0 .. x0+kTbW-1, rows y0 .. y0+H-1) of two fused steps; the whole block calls it.
 template <class S>
 __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
                                         long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
@@ -473,23 +637,39 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int iters = H / 4 + 3;
 
-    // Block k of S(t): row y0 - 2 + 4k + warp, chunks of 4 columns starting at x0 - 4 (periodic).
-    auto load_block = [&](int k) {
+    // Block k of S(t): row y0 - 2 + 4k + warp, kTbChunks chunks of 4 columns starting at x0 - 4.
+    // Lane l copies chunk l (if l < kTbChunks) and chunk l + 32 (if that exists).  Columns wrap
+    // periodically (nx is a multiple of 4, so chunks stay 16-byte aligned; columns of the last
+    // strip past nx hold the periodic continuation of the row).  The chunk columns are fixed for
+    // the tile and the row advances by 4 per block, so both are reduced once and then stepped.
+    auto wrap_x = [&](int c) {
+        int x = (x0 - 4 + 4 * c) % nx;
+        return x < 0 ? x + nx : x;
+    };
+    const bool one_chunk = lane < kTbChunks;
+    const bool two_chunks = lane + 32 < kTbChunks;
+    const int xa = one_chunk ? wrap_x(lane) : 0;
+    const int xb = two_chunks ? wrap_x(lane + 32) : 0;
+    int rcur = (y0 - 2 + warp) % ny;
+    if (rcur < 0) rcur += ny;
+    auto load_block = [&](int k) {  // called once for each k = 0, 1, 2, ... in this order
         const int row = y0 - 2 + 4 * k + warp;
         if (row <= y0 + H + 1) {
-            int r = row % ny;
-            if (r < 0) r += ny;
-            const long long rowoff = (long long)r * nx;
-            for (int c = lane; c < kTbRow / 4; c += 32) {
-                // periodic column (nx is a multiple of 4, so chunks stay 16-byte aligned); columns
-                // of the last strip past nx hold the periodic continuation of the row
-                int x = (x0 - 4 + 4 * c) % nx;
-                if (x < 0) x += nx;
+            const float *rp = src + (long long)rcur * nx;
+            float *sp = r0(k, warp, 0);
+            if (one_chunk) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) cp_async_16(r0(k, warp, i) + 4 * c, src + (long long)i * pitch + rowoff + x);
+                for (int i = 0; i < Q; ++i) cp_async_16(sp + i * kTbRow + 4 * lane, rp + (long long)i * pitch + xa);
+            }
+            if (two_chunks) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    cp_async_16(sp + i * kTbRow + 4 * (lane + 32), rp + (long long)i * pitch + xb);
             }
         }
         cp_async_commit();  // one group per block (empty when nothing is needed)
+        rcur += 4;
+        while (rcur >= ny) rcur -= ny;  // at most two passes: ny >= 3
     };
 #pragma unroll
     for (int k = 0; k < kTbPrefetch; ++k) load_block(k);
@@ -505,13 +685,13 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__
         const int b = y0 + 4 * k - 12 + warp;
         const bool doA = k >= 1 && a <= y0 + H;  // warp-uniform
         const bool doB = k >= 3 && b < y0 + H;
-        float pa[Q][4], pb[Q][4];
+        float pa[Q][kTbV], pb[Q][kTbV];
         if (doB) {
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
                 const int rr = b - cy - (y0 - 5);  // row within the S(t+1) blocks
-                tb_pull4<cx>(r1(rr >> 2, rr & 3, i), lane, pb[i]);
+                tb_pull<cx>(r1(rr >> 2, rr & 3, i), lane, pb[i]);
             });
         }
         if (doA) {
@@ -519,38 +699,41 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
                 const int rr = a - cy - (y0 - 2);  // row within the S(t) blocks
-                tb_pull4<cx>(r0(rr >> 2, rr & 3, i), lane, pa[i]);
+                tb_pull<cx>(r0(rr >> 2, rr & 3, i), lane, pa[i]);
             });
         }
         if (doB) {
-            float post[Q][4];
-            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pb, post, cf); });
-            if (b < ny && x0 + 4 * lane < nx) {
-                float *outp = dst + (long long)b * nx + x0 + 4 * lane;
+            float post[Q][kTbV];
+            collide_chunk<S, kTbPacked>(pb, post, cf);
+            if (b < ny && x0 + kTbV * lane < nx) {
+                float *outp = dst + (long long)b * nx + x0 + kTbV * lane;
 #pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    *reinterpret_cast<float4 *>(outp + (long long)i * pitch) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
+                for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
             }
         }
         if (doA) {
-            float post[Q][4];
-            static_for<4>([&](auto E) { collide_cell<S, decltype(E)::value>(pa, post, cf); });
+            float post[Q][kTbV];
+            collide_chunk<S, kTbPacked>(pa, post, cf);
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                *reinterpret_cast<float4 *>(r1(k, warp, i) + 4 * lane + 4) = make_float4(post[i][0], post[i][1], post[i][2], post[i][3]);
-            // the two halo columns of S(t+1): x0 - 1 (lane 0, offset 3) and x0 + 128 (lane 31, offset 132)
-            if (lane == 0 || lane == 31) {
-                const int off = lane == 0 ? 3 : 132;
-                float p1[Q][1], q1[Q][1];
+            for (int i = 0; i < Q; ++i) tb_st(r1(k, warp, i) + kTbV * lane + 4, post[i]);
+            // the two halo columns of S(t+1), x0 - 1 (offset 3) and x0 + kTbW (offset kTbW + 4),
+            // as one pair in lane 0
+            if (lane == 0) {
+                float p1[Q][2], q1[Q][2];
                 static_for<Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
                     const int rr = a - cy - (y0 - 2);
-                    p1[i][0] = r0(rr >> 2, rr & 3, i)[off - cx];
+                    const float *row = r0(rr >> 2, rr & 3, i);
+                    p1[i][0] = row[3 - cx];
+                    p1[i][1] = row[kTbW + 4 - cx];
                 });
-                collide_cell<S, 0>(p1, q1, cf);
+                collide_chunk<S, kTbPacked>(p1, q1, cf);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) r1(k, warp, i)[off] = q1[i][0];
+                for (int i = 0; i < Q; ++i) {
+                    r1(k, warp, i)[3] = q1[i][0];
+                    r1(k, warp, i)[kTbW + 4] = q1[i][1];
+                }
             }
         }
     }

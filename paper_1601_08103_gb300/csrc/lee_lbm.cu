@@ -267,6 +267,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     h->elem = elem_size(cfg->storage);
     h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
     if (const char *ev = std::getenv("LEE_SINGLE_STEP")) h->single_step_only = ev[0] == '1';
+    if (const char *ev = std::getenv("LEE_FORCE_SCALAR")) h->force_scalar = ev[0] == '1';
+    if (h->force_scalar) h->single_step_only = true;
     const bool is16 = cfg->storage == LEE_STORE_F16 || cfg->storage == LEE_STORE_BF16;
     h->scale = is16 ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -362,7 +364,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.sponge_smax = h->cfg.sponge_strength;
     L.ghost = learned ? h->ghost : nullptr;
     L.ghost_L = learned ? h->ghost_L : 0;
-    L.force_scalar = 0;
+    L.force_scalar = h->force_scalar ? 1 : 0;
     // One time step's launches (boundary network first for the learned edge) on stream `st`.
     auto launch_step = [&](int from, cudaStream_t st) -> cudaError_t {
         L.src = h->buf[from];
