@@ -38,7 +38,7 @@ BYTES_PER_LUP = 2 * 5 * 4  # read + write of q = 5 FP32 populations (algorithmic
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = "2D D2Q5 periodic 2048x2048, FP32, tau=0.6, pulse+8 plane waves, 1000 steps/job"
 PROFILE = os.path.join(ROOT, "profiles", "stream_collide_2step_d2q5_f32_2048x2048.md")
-KERNEL_SOURCES = ["paper_1601_08103_gb300/csrc/kernels.cuh", "paper_1601_08103_gb300/csrc/set_impl.cuh",
+KERNEL_SOURCES = ["paper_1601_08103_gb300/csrc/kernels.cuh", "paper_1601_08103_gb300/csrc/step_launch.cuh",
                   "paper_1601_08103_gb300/csrc/velsets.cuh"]
 
 
@@ -88,10 +88,19 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (at most 3 s) for its first line so that the
+        # samples cover the timed region
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -343,6 +352,69 @@ def forms_3d():
     return {"workload": "3D D3Q7 periodic 384^3, tau=0.55, pulse A=1e-3 w=16, 500 steps", "storage": out}
 
 
+def _device_pulse(shape, amplitude: float, width: float, center):
+    """amplitude * exp(-|x - center|^2 / width^2) with periodic minimum-image distances, built on
+    the device (the large grids below would need gigabytes of host coordinates)."""
+    import torch
+
+    dims = (list(shape) + [1, 1])[:3]
+    r2 = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.float64, device="cuda")
+    for a in range(3):
+        if dims[a] == 1:
+            continue
+        ax = torch.arange(dims[a], dtype=torch.float64, device="cuda")
+        d = torch.remainder(ax - center[a] + dims[a] / 2.0, dims[a]) - dims[a] / 2.0
+        view = [1, 1, 1]
+        view[2 - a] = dims[a]
+        r2 = r2 + (d * d).view(view)
+    return (amplitude * torch.exp(-r2 / (width * width))).reshape(-1)
+
+
+def forms_configs():
+    """The other configurations of the workload table, each timed alone with CUDA events (inputs
+    resident, after a short warm-up): 1D D1Q3 N = 1024 FP64 (on-chip, time per step) and
+    N = 2^28 FP64 (the 1D roofline run), 2D D2Q5 2048^2 FP64, 2D D2Q5 8192^2 FP32 (working set
+    2.7 GB, far beyond L2) and 3D D3Q19 256^3 FP32 (the largest velocity set)."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+
+    runs = [("1d_d1q3_f64_1024", "D1Q3", (1024, 1, 1), "f64", 0.8, 2000, 16.0),
+            ("1d_d1q3_f64_2^28", "D1Q3", (1 << 28, 1, 1), "f64", 0.8, 20, 20.0),
+            ("2d_d2q5_f64_2048", "D2Q5", (2048, 2048, 1), "f64", 0.6, 1000, 32.0),
+            ("2d_d2q5_f32_8192", "D2Q5", (8192, 8192, 1), "f32", 0.6, 1000, 32.0),
+            ("3d_d3q19_f32_256", "D3Q19", (256, 256, 256), "f32", 0.55, 100, 16.0)]
+    out = {}
+    stream = torch.cuda.current_stream()
+    for key, name, shape, storage, tau, steps, w in runs:
+        info = lee.lee_velset_info(name)
+        cells = int(np.prod(shape))
+        rho = _device_pulse(shape, 1e-3, w, [n / 2.7 for n in shape])
+        u = torch.zeros((info["D"], cells), dtype=torch.float64, device="cuda")
+        th = torch.zeros(cells, dtype=torch.float64, device="cuda")
+        with lee.Solver(name, shape, tau, storage=storage, stream=stream) as sv:
+            sv.init_fields(rho, u, th)
+            sv.step(4)
+            sv.init_fields(rho, u, th)
+            del rho, u, th
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sv.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            finite = sv.check_finite()
+            spl = sv.steps_per_launch
+        bpl = 2 * info["q"] * lee.STORAGE_BYTES[storage]
+        out[key] = {"cells": cells, "steps": steps, "ms": round(ms, 3), "us_per_step": round(ms * 1e3 / steps, 3),
+                    "mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
+                    "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "bytes_per_lup": bpl,
+                    "steps_per_launch": spl, "finite": bool(finite)}
+        torch.cuda.empty_cache()
+    return out
+
+
 def forms_batched(steps: int = 1000):
     """Batched 2D form: 96 periodic D2Q5 domains (sizes from {128, ..., 1024}^2, tau in
     [0.52, 1.2], one pulse each, seed 4), FP32, `steps` steps, in one batched launch per step
@@ -500,7 +572,7 @@ def run_reference(args, rank, world):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true")
@@ -523,6 +595,7 @@ def main(argv=None):
             line["cpu_baseline"] = cpu_baseline()
         if world == 1 and not args.no_forms:
             line["forms"] = forms_3d()
+            line["forms_configs"] = forms_configs()
             line["forms_batched"] = forms_batched()
             line["forms_learned"] = forms_learned()
         print(json.dumps(line), flush=True)

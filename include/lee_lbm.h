@@ -219,7 +219,7 @@ lee_status lee_lbm_destroy(lee_lbm *h);
  *   cells: 1 .. 2^31 - 1; pitch >= cells (elements between velocity arrays);
  *   store_scale: S for 16-bit storage (> 0), ignored otherwise;
  *   out: DEVICE pointer to D + 4 doubles; cuda_stream: stream to run on (NULL = default).
- * Scratch: a fixed file-scope device array of 2432 x 8 FP64 block partials (155,648 bytes) that
+ * Scratch: a fixed file-scope device array of 2432 x 16 FP64 block partials (311,296 bytes) that
  * every GPU loading the library keeps until the process exits.  Sizes beyond it (more than
  * 2^31 - 1 cells) are rejected with LEE_ERR_INVALID_ARGUMENT; so are bad pointers or enums.
  * Set-up: the first call on a device (with that device current) looks up the array's device

@@ -11,17 +11,75 @@ namespace lee {
 // auxiliary kernels: equilibrium initialisation, moments, reductions, FP64 import/export
 // ---------------------------------------------------------------------------------------------
 
-// Per-set FP64 constants for the auxiliary kernels (general form of Sec. 5).
+// Per-set FP64 constants for the auxiliary kernels (general form of Sec. 5).  The kernels work
+// on per-shell sums (every weight and coefficient depends on the shell |c_i|^2 only), so the
+// shell factors are folded on the host and each population costs one or two FP64 additions:
+//   g_i^eq = eqA[.][s] rho' + eqB[.][s] theta' + eqC[.][s] (c_i . u')   (i in shell s;
+//            [0] the population itself, [1] the scaled 16-bit value S g_i / f*_s, per unit S),
+//   with eqA = F (a1 + s c1 / 2), eqB = F (a2 + s c2 / 2), eqC = F b, F = f*_s resp. 1;
+//   a stored 16-bit value decodes as g = dec[s] x stored, dec = f*_s / S (enc = 1 / dec);
+//   the energy moment weight of shell s is ew[s] = (s + beta_s) / 2;
+//   u' = j / rho0 and theta' = kE e - kR rho' with kE = (gamma - 1) / rho0, kR = theta0 / rho0.
+// (|c|^2 = s for every velocity of shell s.)
 struct SetConsts {
     double rho0, theta0, gamma, a1, a2, b, c1, c2;
     double f[4];     // f* per shell
     double beta[4];  // beta per shell
     double scale;    // 16-bit storage scale S (1 otherwise)
+    double eqA[2][4], eqB[2][4], eqC[2][4];
+    double dec[4], enc[4], ew[4];
+    double inv_rho0, kE, kR;
 };
+
+// Shells present in set S, in increasing order, and the compact slot of shell s.
+template <class S>
+__host__ __device__ constexpr int n_shells() {
+    int n = 0;
+    for (int s = 0; s < 4; ++s) n += shell_present<S>(s) ? 1 : 0;
+    return n;
+}
+template <class S>
+__host__ __device__ constexpr int shell_slot(int s) {
+    int n = 0;
+    for (int t = 0; t < s; ++t) n += shell_present<S>(t) ? 1 : 0;
+    return n;
+}
 
 template <class S>
 __device__ __forceinline__ double decode(double stored, int i, const SetConsts &k, bool scaled) {
-    return scaled ? stored * (k.f[S::shell(i)] / k.scale) : stored;
+    return scaled ? stored * k.dec[S::shell(i)] : stored;
+}
+
+// g_i^eq of one cell for every velocity: per shell two products, per velocity the signed sum of
+// the velocity components it moves along and one fused multiply-add.
+template <class S, int SC, class F>
+__device__ __forceinline__ void equilibrium_cell(double r, double th, const double (&uu)[3], const SetConsts &k, F &&put) {
+    double base[4];
+    static_for<4>([&](auto Sx) {
+        constexpr int s = decltype(Sx)::value;
+        if constexpr (shell_present<S>(s)) base[s] = fma(k.eqB[SC][s], th, k.eqA[SC][s] * r);
+    });
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int s = S::shell(i);
+        constexpr bool moving = S::c(i, 0) != 0 || S::c(i, 1) != 0 || S::c(i, 2) != 0;
+        if constexpr (!moving) {
+            put(i, base[s]);
+        } else {
+            double cu = 0.0;
+            bool first = true;
+            static_for<3>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                constexpr int c = S::c(i, a);
+                if constexpr (c != 0) {
+                    const double t = c == 1 ? uu[a] : -uu[a];
+                    cu = first ? t : cu + t;
+                    first = false;
+                }
+            });
+            put(i, fma(k.eqC[SC][s], cu, base[s]));
+        }
+    });
 }
 
 // g_i = g_i^eq(rho', u', theta') (Sec. 7 initial condition), encoded into storage type T.
@@ -29,20 +87,13 @@ template <class S, class T>
 __global__ void k_init_equilibrium(const double *__restrict__ rho, const double *__restrict__ u,
                                    const double *__restrict__ theta, T *__restrict__ g, long long cells, long long pitch,
                                    SetConsts k) {
-    constexpr bool scaled = Store<T>::scaled;
+    constexpr int SC = Store<T>::scaled ? 1 : 0;
     for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
-        const double r = rho[x], th = theta[x];
         double uu[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int a = 0; a < S::D; ++a) uu[a] = u[(long long)a * cells + x];
-        static_for<S::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int s = S::shell(i);
-            double cu = 0.0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) cu += S::c(i, a) * uu[a];
-            const double bracket = k.a1 * r + k.a2 * th + k.b * cu + 0.5 * (double)s * (k.c1 * r + k.c2 * th);
-            const double v = scaled ? bracket * k.scale : bracket * k.f[s];
+        equilibrium_cell<S, SC>(rho[x], theta[x], uu, k, [&](int i, double v) {
+            if (SC) v *= k.scale;
             g[(long long)i * pitch + x] = Store<T>::make((typename Store<T>::C)v);
         });
     }
@@ -56,19 +107,10 @@ __global__ void k_init_maxabs(const double *__restrict__ rho, const double *__re
                               unsigned int *__restrict__ maxbits) {
     float m = 0.f;
     for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
-        const double r = rho[x], th = theta[x];
         double uu[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int a = 0; a < S::D; ++a) uu[a] = u[(long long)a * cells + x];
-        static_for<S::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int s = S::shell(i);
-            double cu = 0.0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) cu += S::c(i, a) * uu[a];
-            const double bracket = k.a1 * r + k.a2 * th + k.b * cu + 0.5 * (double)s * (k.c1 * r + k.c2 * th);
-            m = fmaxf(m, (float)fabs(bracket));
-        });
+        equilibrium_cell<S, 1>(rho[x], theta[x], uu, k, [&](int, double v) { m = fmaxf(m, (float)fabs(v)); });
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
@@ -96,78 +138,147 @@ __global__ void k_sponge_damp(T *__restrict__ g, GridDesc gd, int w, typename St
     }
 }
 
+// Per-shell sums of one cell's stored populations: P[slot] = sum g, J[slot][a] = sum c_a g (in
+// stored units), and whether every value is finite.
+template <class S, class T>
+__device__ __forceinline__ bool shell_sums(const T *__restrict__ g, long long pitch, long long x,
+                                           double (&P)[n_shells<S>()], double (&J)[n_shells<S>()][3],
+                                           double (&Sq)[n_shells<S>()]) {
+    bool finite = true;
+    static_for<n_shells<S>()>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        P[k] = 0.0;
+        Sq[k] = 0.0;
+        J[k][0] = J[k][1] = J[k][2] = 0.0;
+    });
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int k = shell_slot<S>(S::shell(i));
+        const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+        finite = finite && isfinite(v);
+        P[k] += v;
+        Sq[k] = fma(v, v, Sq[k]);
+        static_for<3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (S::c(i, a) == 1) J[k][a] += v;
+            if constexpr (S::c(i, a) == -1) J[k][a] -= v;
+        });
+    });
+    return finite;
+}
+
 // Per-cell moments (Sec. 4 discrete moments, Sec. 5 temperature) in FP64.
 template <class S, class T>
 __global__ void k_moments(const T *__restrict__ g, long long cells, long long pitch, SetConsts k, double *__restrict__ rho,
                           double *__restrict__ u, double *__restrict__ theta) {
     constexpr bool scaled = Store<T>::scaled;
+    constexpr int NS = n_shells<S>();
     for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
+        double P[NS], J[NS][3], Sq[NS];
+        shell_sums<S, T>(g, pitch, x, P, J, Sq);
         double r = 0.0, e = 0.0, j[3] = {0.0, 0.0, 0.0};
-        static_for<S::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int s = S::shell(i);
-            const double v = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
-            r += v;
+        static_for<4>([&](auto Sx) {
+            constexpr int s = decltype(Sx)::value;
+            if constexpr (shell_present<S>(s)) {
+                constexpr int kk = shell_slot<S>(s);
+                const double p = scaled ? P[kk] * k.dec[s] : P[kk];
+                r += p;
+                e = fma(k.ew[s], p, e);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) j[a] += S::c(i, a) * v;
-            e += 0.5 * ((double)s + k.beta[s]) * v;
+                for (int a = 0; a < S::D; ++a) j[a] += scaled ? J[kk][a] * k.dec[s] : J[kk][a];
+            }
         });
         if (rho) rho[x] = r;
         if (u) {
 #pragma unroll
-            for (int a = 0; a < S::D; ++a) u[(long long)a * cells + x] = j[a] / k.rho0;
+            for (int a = 0; a < S::D; ++a) u[(long long)a * cells + x] = j[a] * k.inv_rho0;
         }
-        if (theta) theta[x] = ((k.gamma - 1.0) * e - k.theta0 * r) / k.rho0;
+        if (theta) theta[x] = fma(k.kE, e, -k.kR * r);
     }
 }
 
 constexpr int kReduceThreads = 256;
-constexpr int kReduceMax = 8;  // D + 4 <= 7 values, padded
+constexpr int kReduceMax = 16;  // raw accumulators per block (<= 16, see reduce_nraw)
 
-// Block partial sums of the D + 4 diagnostics (see lee_lbm_reduce), fixed order per block.
+// Raw accumulators of a reduction, per block: for every present shell (compact slot k)
+//   [k] = sum g,  [NS + k] = sum g^2,  [2 NS + k D + a] = sum c_a g   (stored units),
+// and [NR - 1] = number of non-finite values.  The weights come in when the block sums are
+// combined (k_reduce_final): the paper's diagnostics are linear in these shell sums.
+template <class S>
+__host__ __device__ constexpr int reduce_nraw() {
+    return 2 * n_shells<S>() + n_shells<S>() * S::D + 1;
+}
+
 template <class S, class T>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__restrict__ g, long long cells, long long pitch,
-                                                                   SetConsts k, double *__restrict__ partial) {
-    constexpr bool scaled = Store<T>::scaled;
-    constexpr int NV = S::D + 4;
-    double acc[NV];
+                                                                   double *__restrict__ partial) {
+    constexpr int NS = n_shells<S>(), D = S::D, NR = reduce_nraw<S>();
+    static_assert(NR <= kReduceMax, "raw accumulators do not fit");
+    double acc[NR];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < NR; ++v) acc[v] = 0.0;
     for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
-        static_for<S::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int s = S::shell(i);
-            const double v = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
-            if (!isfinite(v)) {
-                acc[NV - 1] += 1.0;
-            } else {
-                acc[0] += v;
+        double P[NS], J[NS][3], Sq[NS];
+        if (!shell_sums<S, T>(g, pitch, x, P, J, Sq)) {
+            // count the non-finite values of this cell; its finite ones still add up
+            static_for<S::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+                if (!isfinite(v)) acc[NR - 1] += 1.0;
+            });
+            static_for<S::Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int k = shell_slot<S>(S::shell(i));
+                const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+                if (isfinite(v)) {
+                    acc[k] += v;
+                    acc[NS + k] = fma(v, v, acc[NS + k]);
+                    static_for<D>([&](auto A) {
+                        constexpr int a = decltype(A)::value;
+                        if constexpr (S::c(i, a) == 1) acc[2 * NS + k * D + a] += v;
+                        if constexpr (S::c(i, a) == -1) acc[2 * NS + k * D + a] -= v;
+                    });
+                }
+            });
+            continue;
+        }
+        static_for<NS>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            acc[k] += P[k];
+            acc[NS + k] += Sq[k];
 #pragma unroll
-                for (int a = 0; a < S::D; ++a) acc[1 + a] += S::c(i, a) * v;
-                acc[S::D + 1] += 0.5 * ((double)s + k.beta[s]) * v;
-                acc[S::D + 2] += v * v / k.f[s];
-            }
+            for (int a = 0; a < D; ++a) acc[2 * NS + k * D + a] += J[k][a];
         });
     }
-    __shared__ double sh[kReduceThreads / 32][NV];
+    __shared__ double sh[kReduceThreads / 32][NR];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < NR; ++v) {
         double a = acc[v];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
         if (lane == 0) sh[warp][v] = a;
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
+    if (threadIdx.x < NR) {
         double a = 0.0;
         for (int w = 0; w < kReduceThreads / 32; ++w) a += sh[w][threadIdx.x];
         partial[(long long)blockIdx.x * kReduceMax + threadIdx.x] = a;
     }
 }
 
-// Ordered sum of the block partials (one warp per output value).
-__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out);
+// How the raw block sums combine into the D + 4 diagnostics of lee_lbm_reduce:
+//   sum rho' = sum_k dec_k P_k, sum j_a = sum_k dec_k J_ka, energy moment = sum_k ew_k dec_k P_k,
+//   weighted energy = sum_k dec_k^2 Sq_k / f*_k, non-finite count (dec_k = 1 unless the storage
+//   is scaled).
+struct ReduceCombine {
+    int D, ns, nraw;
+    double dec[4], ew[4], f[4];  // per compact slot
+};
+
+// Ordered sum of the block partials (one warp per raw value) and the combination above; one
+// block of 32 * nraw threads.
+__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, ReduceCombine c, double *__restrict__ out);
 
 // FP64 [q][cells] <-> storage (checkpoint export / import).
 template <class S, class T>
@@ -189,7 +300,7 @@ __global__ void k_import(const double *__restrict__ in, long long cells, long lo
             constexpr int i = decltype(I)::value;
             constexpr int s = S::shell(i);
             const double v = in[(long long)i * cells + x];
-            const double st = scaled ? v * (k.scale / k.f[s]) : v;
+            const double st = scaled ? v * k.enc[s] : v;
             g[(long long)i * pitch + x] = Store<T>::make((typename Store<T>::C)st);
         });
     }

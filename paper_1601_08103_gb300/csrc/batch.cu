@@ -542,11 +542,12 @@ lee_status lee_batch_reduce(lee_batch *b, int32_t d, double *out, int32_t on_dev
     if (d < 0 || d >= b->count || !out) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "reduce: bad args");
     const long long c = b->cells[d];
     const int nblocks = aux_blocks(c, kReduceThreads);
-    BCK(b, b->ops->reduce_partial(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], consts_for(b->set, 1.0), b->partial,
-                                  nblocks, b->st),
+    const SetConsts k = consts_for(b->set, 1.0);
+    BCK(b, b->ops->reduce_partial(b->storage, dom_ptr(b, b->cur, d), c, b->pitch[d], k, b->partial, nblocks, b->st),
         "reduce_partial");
     double *dst = on_device ? out : b->red_out;
-    k_reduce_final<<<6, 32, 0, b->st>>>(b->partial, nblocks, 6, dst);
+    const ReduceCombine rc = make_reduce_combine(b->ops, k, false);
+    k_reduce_final<<<1, 32 * rc.nraw, 0, b->st>>>(b->partial, nblocks, rc, dst);
     BCK(b, cudaGetLastError(), "reduce_final");
     if (!on_device) {
         BCK(b, cudaMemcpyAsync(out, b->red_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, b->st), "D2H reduce");

@@ -35,14 +35,32 @@ const SetOps *set_ops(int set) {
     }
 }
 
-__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out) {
-    const int v = blockIdx.x;  // one block (one warp) per output value
-    if (v >= nv) return;
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 32) a += partial[(long long)b * kReduceMax + v];
+__global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, ReduceCombine c, double *__restrict__ out) {
+    __shared__ double raw[kReduceMax];
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (v < c.nraw) {
+        double a = 0.0;
+        for (int b = lane; b < nblocks; b += 32) a += partial[(long long)b * kReduceMax + v];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
-    if (threadIdx.x == 0) out[v] = a;
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
+        if (lane == 0) raw[v] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int ns = c.ns, D = c.D;
+    double r = 0.0, e = 0.0, w = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < ns; ++k) {
+        const double p = raw[k] * c.dec[k];
+        r += p;
+        e += c.ew[k] * p;
+        w += raw[ns + k] * (c.dec[k] * c.dec[k]) / c.f[k];
+        for (int a = 0; a < D; ++a) j[a] += raw[2 * ns + k * D + a] * c.dec[k];
+    }
+    out[0] = r;
+    for (int a = 0; a < D; ++a) out[1 + a] = j[a];
+    out[D + 1] = e;
+    out[D + 2] = w;
+    out[D + 3] = raw[c.nraw - 1];
 }
 
 SetConsts consts_for(int set, double scale) {
@@ -471,7 +489,9 @@ lee_status lee_lbm_reduce(lee_lbm *h, double *out, int32_t on_device) {
     LEE_CK(h, h->ops->reduce_partial(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, h->partial, h->nblocks, h->st),
            "reduce_partial");
     double *dst = on_device ? out : h->red_out;
-    k_reduce_final<<<nv, 32, 0, h->st>>>(h->partial, h->nblocks, nv, dst);
+    const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
+    const ReduceCombine rc = make_reduce_combine(h->ops, k, is16);
+    k_reduce_final<<<1, 32 * rc.nraw, 0, h->st>>>(h->partial, h->nblocks, rc, dst);
     LEE_CK(h, cudaGetLastError(), "reduce_final");
     if (!on_device) {
         LEE_CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->st), "D2H reduce");

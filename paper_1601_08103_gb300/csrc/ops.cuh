@@ -106,7 +106,41 @@ SetConsts host_consts(double scale) {
         k.beta[s] = S::betas(s);
     }
     k.scale = scale;
+    for (int s = 0; s < 4; ++s) {
+        const double fa = k.a1 + 0.5 * s * k.c1, fb = k.a2 + 0.5 * s * k.c2;
+        k.eqA[0][s] = k.f[s] * fa;
+        k.eqB[0][s] = k.f[s] * fb;
+        k.eqC[0][s] = k.f[s] * k.b;
+        k.eqA[1][s] = fa;
+        k.eqB[1][s] = fb;
+        k.eqC[1][s] = k.b;
+        k.dec[s] = k.f[s] / scale;
+        k.enc[s] = k.f[s] > 0.0 ? scale / k.f[s] : 0.0;
+        k.ew[s] = 0.5 * (s + k.beta[s]);
+    }
+    k.inv_rho0 = 1.0 / k.rho0;
+    k.kE = (k.gamma - 1.0) / k.rho0;
+    k.kR = k.theta0 / k.rho0;
     return k;
+}
+
+// Combination of the raw per-shell block sums of k_reduce_partial (see ReduceCombine).
+inline ReduceCombine make_reduce_combine(const SetOps *o, const SetConsts &k, bool scaled) {
+    ReduceCombine c{};
+    bool present[4] = {false, false, false, false};
+    for (int i = 0; i < o->Q; ++i) present[o->shell[i]] = true;
+    int n = 0;
+    for (int s = 0; s < 4; ++s) {
+        if (!present[s]) continue;
+        c.dec[n] = scaled ? k.dec[s] : 1.0;
+        c.ew[n] = k.ew[s];
+        c.f[n] = k.f[s];
+        ++n;
+    }
+    c.D = o->D;
+    c.ns = n;
+    c.nraw = 2 * n + n * o->D + 1;
+    return c;
 }
 
 // Grid size for grid-stride auxiliary kernels.

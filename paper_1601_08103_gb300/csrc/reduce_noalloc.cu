@@ -9,8 +9,8 @@
 // scratch; this one takes the populations and the output directly and keeps its scratch in a
 // fixed file-scope device array instead.
 //
-// The scratch: kMaxPartials block partials x kReduceMax values in FP64 (2432 x 8 x 8 B =
-// 155,648 bytes).  Every GPU that loads the library holds this array until the process exits.
+// The scratch: kMaxPartials block partials x kReduceMax values in FP64 (2432 x 16 x 8 B =
+// 311,296 bytes).  Every GPU that loads the library holds this array until the process exits.
 // The launch shape is the one lee_lbm_reduce uses (min(ceil(cells / 256), 2432) blocks of 256
 // threads, grid-stride), so the two entry points sum in the same order and agree bit for bit.
 #include <cuda_runtime.h>
@@ -74,8 +74,8 @@ extern "C" lee_status lee_reduce_noalloc(int32_t set, int32_t storage, const voi
     // Each block overwrites its own partials before the final pass reads them, so nothing in the
     // shared scratch has to be cleared between calls.
     if (o->reduce_partial(storage, g, cells, pitch, k, partials, nblocks, st) != cudaSuccess) return LEE_ERR_CUDA;
-    const int nv = o->D + 4;
-    k_reduce_final<<<nv, 32, 0, st>>>(partials, nblocks, nv, out);
+    const ReduceCombine rc = make_reduce_combine(o, k, is16);
+    k_reduce_final<<<1, 32 * rc.nraw, 0, st>>>(partials, nblocks, rc, out);
     if (cudaGetLastError() != cudaSuccess) return LEE_ERR_CUDA;
     return LEE_OK;
 }

@@ -1,61 +1,9 @@
 // set_impl.cuh -- host launchers for one velocity set, instantiated by the set_*.cu units.
 #pragma once
 
-#include "ops.cuh"
+#include "step_launch.cuh"
 
 namespace lee {
-
-template <class S, class T, int V, bool OPEN>
-cudaError_t launch_step_v(const StepLaunch &L) {
-    using C = typename Store<T>::C;
-    GridDesc gd;
-    gd.nx = L.nx;
-    gd.ny = L.ny;
-    gd.nz = L.nz;
-    gd.nxc = L.nx / V;
-    gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
-    gd.pitch = L.pitch;
-    const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
-    OpenEdge<C> ob;
-    ob.sponge_w = L.sponge_w;
-    ob.sponge_smax = (C)L.sponge_smax;
-    ob.ghost = static_cast<const C *>(L.ghost);
-    ob.ghost_L = L.ghost_L;
-    const long long blocks = (gd.nchunks + 255) / 256;
-    k_stream_collide<S, T, V, OPEN><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
-                                                                              static_cast<T *>(L.dst), gd, cf, ob);
-    return cudaGetLastError();
-}
-
-// Vector width: one 16-byte access per velocity and thread (8 bytes for the 19-velocity set, to
-// bound register use); one cell per thread when nx is not a multiple of the width.
-template <class S, class T>
-constexpr int vec_width() {
-    constexpr int bytes = (S::Q > 13) ? 8 : 16;
-    constexpr int v = bytes / (int)sizeof(T);
-    return v < 1 ? 1 : v;
-}
-
-template <class S, class T>
-cudaError_t launch_step_t(const StepLaunch &L) {
-    constexpr int V = vec_width<S, T>();
-    if constexpr (V > 1) {
-        if (!L.force_scalar && L.nx % V == 0)
-            return L.open ? launch_step_v<S, T, V, true>(L) : launch_step_v<S, T, V, false>(L);
-    }
-    return L.open ? launch_step_v<S, T, 1, true>(L) : launch_step_v<S, T, 1, false>(L);
-}
-
-template <class Fn>
-cudaError_t with_storage(int storage, Fn &&fn) {
-    switch (storage) {
-    case LEE_STORE_F64: return fn((double *)nullptr);
-    case LEE_STORE_F32: return fn((float *)nullptr);
-    case LEE_STORE_F16: return fn((__half *)nullptr);
-    case LEE_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
-    default: return cudaErrorInvalidValue;
-    }
-}
 
 template <class S>
 struct SetImpl {
@@ -90,7 +38,7 @@ struct SetImpl {
                                       double *partial, int nblocks, cudaStream_t st) {
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
-            k_reduce_partial<S, T><<<nblocks, kReduceThreads, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, partial);
+            k_reduce_partial<S, T><<<nblocks, kReduceThreads, 0, st>>>(static_cast<const T *>(g), cells, pitch, partial);
             return cudaGetLastError();
         });
     }
@@ -141,57 +89,8 @@ struct SetImpl {
             });
         }
     }
-    // Resident capacity of the two-step kernel (blocks per SM x SMs) per device, set by
-    // step2_prepare outside any stream capture.
-    static int *step2_capacity() {
-        static int cap[64] = {0};
-        return cap;
-    }
-    static cudaError_t step2_prepare() {
-        if constexpr (S::D != 2) {
-            return cudaErrorInvalidValue;
-        } else {
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e != cudaSuccess) return e;
-            if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-            if (step2_capacity()[dev]) return cudaSuccess;
-            constexpr int smem = tb_smem_bytes<S>();
-            e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step<S>, 128, smem);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            step2_capacity()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
-            return cudaSuccess;
-        }
-    }
-    static cudaError_t step2(const StepLaunch &L) {
-        if constexpr (S::D != 2) {
-            return cudaErrorInvalidValue;
-        } else {
-            if (L.storage != LEE_STORE_F32 || L.open || L.nx % 4 != 0 || L.ny < 3) return cudaErrorInvalidValue;
-            const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
-            constexpr int smem = tb_smem_bytes<S>();
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e != cudaSuccess) return e;
-            if (dev < 0 || dev >= 64 || step2_capacity()[dev] == 0) return cudaErrorNotReady;  // prepare first
-            // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
-            const int strips = (L.nx + kTbW - 1) / kTbW;
-            int segs = step2_capacity()[dev] / strips;
-            if (segs < 1) segs = 1;
-            int H = (L.ny + segs - 1) / segs;
-            H = (H + 3) / 4 * 4;
-            if (H < 16) H = 16;
-            const dim3 grid(strips, (L.ny + H - 1) / H);
-            k_stream_collide_2step<S><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
-                                                                     static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, H,
-                                                                     cf);
-            return cudaGetLastError();
-        }
-    }
+    static cudaError_t step2_prepare() { return two_step_prepare<S>(); }
+    static cudaError_t step2(const StepLaunch &L) { return two_step_launch<S>(L); }
     static SetOps make() {
         SetOps o{};
         o.D = S::D;

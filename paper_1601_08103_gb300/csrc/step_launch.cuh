@@ -1,0 +1,118 @@
+// step_launch.cuh -- launch configuration of the fused stream-collide kernels for one velocity set:
+// the one-step kernel (cells per thread, grid) and the two-step kernel (tile height from the
+// resident capacity).  Together with kernels.cuh and velsets.cuh this fixes what the profiled
+// hot-path launches execute.
+#pragma once
+
+#include "ops.cuh"
+
+namespace lee {
+
+template <class S, class T, int V, bool OPEN>
+cudaError_t launch_step_v(const StepLaunch &L) {
+    using C = typename Store<T>::C;
+    GridDesc gd;
+    gd.nx = L.nx;
+    gd.ny = L.ny;
+    gd.nz = L.nz;
+    gd.nxc = L.nx / V;
+    gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
+    gd.pitch = L.pitch;
+    const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
+    OpenEdge<C> ob;
+    ob.sponge_w = L.sponge_w;
+    ob.sponge_smax = (C)L.sponge_smax;
+    ob.ghost = static_cast<const C *>(L.ghost);
+    ob.ghost_L = L.ghost_L;
+    const long long blocks = (gd.nchunks + 255) / 256;
+    k_stream_collide<S, T, V, OPEN><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
+                                                                              static_cast<T *>(L.dst), gd, cf, ob);
+    return cudaGetLastError();
+}
+
+// Vector width: one 16-byte access per velocity and thread (8 bytes for the 19-velocity set, to
+// bound register use); one cell per thread when nx is not a multiple of the width.
+template <class S, class T>
+constexpr int vec_width() {
+    constexpr int bytes = (S::Q > 13) ? 8 : 16;
+    constexpr int v = bytes / (int)sizeof(T);
+    return v < 1 ? 1 : v;
+}
+
+template <class S, class T>
+cudaError_t launch_step_t(const StepLaunch &L) {
+    constexpr int V = vec_width<S, T>();
+    if constexpr (V > 1) {
+        if (!L.force_scalar && L.nx % V == 0)
+            return L.open ? launch_step_v<S, T, V, true>(L) : launch_step_v<S, T, V, false>(L);
+    }
+    return L.open ? launch_step_v<S, T, 1, true>(L) : launch_step_v<S, T, 1, false>(L);
+}
+
+template <class Fn>
+cudaError_t with_storage(int storage, Fn &&fn) {
+    switch (storage) {
+    case LEE_STORE_F64: return fn((double *)nullptr);
+    case LEE_STORE_F32: return fn((float *)nullptr);
+    case LEE_STORE_F16: return fn((__half *)nullptr);
+    case LEE_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Resident capacity of the two-step kernel (blocks per SM x SMs) per device, set by
+// two_step_prepare outside any stream capture.
+template <class S>
+int *two_step_capacity() {
+    static int cap[64] = {0};
+    return cap;
+}
+template <class S>
+cudaError_t two_step_prepare() {
+    if constexpr (S::D != 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (two_step_capacity<S>()[dev]) return cudaSuccess;
+        constexpr int smem = tb_smem_bytes<S>();
+        e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step<S>, 128, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        two_step_capacity<S>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+        return cudaSuccess;
+    }
+}
+template <class S>
+cudaError_t two_step_launch(const StepLaunch &L) {
+    if constexpr (S::D != 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (L.storage != LEE_STORE_F32 || L.open || L.nx % 4 != 0 || L.ny < 3) return cudaErrorInvalidValue;
+        const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
+        constexpr int smem = tb_smem_bytes<S>();
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || two_step_capacity<S>()[dev] == 0) return cudaErrorNotReady;  // prepare first
+        // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
+        const int strips = (L.nx + kTbW - 1) / kTbW;
+        int segs = two_step_capacity<S>()[dev] / strips;
+        if (segs < 1) segs = 1;
+        int H = (L.ny + segs - 1) / segs;
+        H = (H + 3) / 4 * 4;
+        if (H < 16) H = 16;
+        const dim3 grid(strips, (L.ny + H - 1) / H);
+        k_stream_collide_2step<S><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
+                                                                 static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, H,
+                                                                 cf);
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace lee

@@ -372,3 +372,33 @@ def test_vector_and_packed_paths_equal_the_scalar_path(gpu_lib, monkeypatch, nam
             sv.get_populations(g)
             outs.append(g)
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("name", ["D2Q5", "D3Q19"])
+def test_nonfinite_values_are_counted_and_left_out(gpu_lib, name, storage):
+    """Planted NaN / +-Inf populations: the reduction counts them and sums every finite value
+    like the oracle does; check_finite reports them; a clean state reports none."""
+    lee = gpu_lib
+    s = oracle.velset(name)
+    shape = shapes_for(s.D, True)[0]
+    cells = int(np.prod(shape))
+    p = perm_to_lib(lee, name)
+    g = inputs.random_populations(s.q, cells, seed=31)  # taken as library order
+    with lee.Solver(name, shape, 0.6, storage=storage, store_scale=1024.0) as sv:
+        sv.set_populations(g)
+        assert sv.check_finite()
+        bad = [(0, 5, np.nan), (s.q - 1, cells - 1, np.inf), (1, cells // 2, -np.inf), (2, 7, np.nan)]
+        gb = g.copy()
+        for i, x, v in bad:
+            gb[i, x] = v
+        sv.set_populations(gb)
+        stored = np.empty((s.q, cells))
+        sv.get_populations(stored)  # the values as stored (rounded for 16-bit storage)
+        red = np.empty(s.D + 4)
+        sv.reduce(red)
+        assert not sv.check_finite()
+    assert red[-1] == len(bad)
+    want = oracle.reduce(name, stored[np.argsort(p)])  # back to the oracle's order
+    assert want[-1] == len(bad)
+    np.testing.assert_allclose(red[:-1], want[:-1], rtol=1e-12, atol=1e-15 * np.abs(stored[np.isfinite(stored)]).sum())
