@@ -490,6 +490,7 @@ CASES = {
     "d3q7_f16": ("D3Q7", (384, 384, 384), "f16", 0.55),
     "d3q7_bf16": ("D3Q7", (384, 384, 384), "bf16", 0.55),
     "d3q19_f32": ("D3Q19", (256, 256, 256), "f32", 0.55),
+    "d2q5_f32_4096": ("D2Q5", (4096, 4096, 1), "f32", 0.6),
     "d2q5_f32_8192": ("D2Q5", (8192, 8192, 1), "f32", 0.6),
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
     "d3q7_f32_odd": ("D3Q7", (385, 383, 381), "f32", 0.55),

@@ -545,66 +545,54 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 // ---------------------------------------------------------------------------------------------
 // two time steps per launch (temporal blocking) for periodic 2D FP32 grids with nx % 4 == 0
 // ---------------------------------------------------------------------------------------------
-// A block (4 warps) owns an output tile of kTbW columns x H rows (H a multiple of 4, chosen by
-// the host so that all tiles are resident at once) and marches down it four rows per iteration,
-// one row per warp, kTbV = kTbW / 32 cells per lane.  Output row b at t+2 needs S(t+1) on rows
-// b-1..b+1 and columns x0-1..x0+kTbW, which needs S(t) on rows b-2..b+2 and columns
-// x0-2..x0+kTbW+1.  Per iteration k (row blocks of 4):
-//   L_k: S(t) rows y0-2+4k .. y0+1+4k stream in by 16-byte cp.async, kTbPrefetch blocks ahead,
-//        into a 4-block ring (columns x0-4 .. x0+kTbW+3, so every chunk is 16-byte aligned);
-//   A_k: S(t+1) rows y0+4k-5 .. y0+4k-2 from L_{k-1}, L_k into a 3-block ring;
-//   B_k: S(t+2) rows y0+4k-12 .. y0+4k-9 from A_{k-2}, A_{k-1}, stored to global memory.
-// B_k does not read A_k, so one barrier per iteration separates all producers and consumers.
-// S(t+1) is kept in the storage type, so every value is rounded exactly as in two single steps:
-// the result equals them bit for bit.  DRAM sees one read and one write of every population per
-// two steps, plus halo rows that neighbouring tiles (running at the same time) mostly take from L2.
-// The rings take (4 + 3) * 4 * q * (kTbW + 8) floats of shared memory per block, which sets how
-// many blocks (and warps) an SM holds: 76 KB and 3 blocks for D2Q5 at kTbW = 128, 40 KB and 5
-// blocks at kTbW = 64.
-constexpr int kTbW = 128, kTbPrefetch = 2;
+// A block (4 warps) owns an output tile of kTbW = 128 columns x H rows (H a multiple of 4, chosen
+// by the host so that all tiles are resident at once) and marches down it four rows per
+// iteration, one row per warp, four cells (one float4) per lane.  Output row b at t+2 needs
+// S(t+1) on rows b-1..b+1 and columns x0-1..x0+128, which needs S(t) on rows b-2..b+2 and
+// columns x0-2..x0+129.  Per iteration k (rows relative to the tile):
+//   A_k: S(t+1) rows 4k-1 .. 4k+2 (one per warp) are pulled from S(t) in global memory exactly as
+//        in the one-step kernel (aligned float4 loads of rows y - c_y, x-neighbours by warp
+//        shuffle, the two edge columns by scalar loads), collided, and written to slot k of a
+//        3-slot shared-memory ring of 4-row blocks, together with the halo columns x0-1 and
+//        x0+128 (one f32x2 pair in lane 0);
+//   barrier;
+//   B_k: S(t+2) rows 4k-4 .. 4k-1 are pulled from ring slots k-1 and k, collided and stored.
+// A_{k+1} writes slot k+1, which no B_k reads, so one barrier per iteration separates every
+// producer from its consumers, and the tile needs H/4 + 1 iterations.  S(t+1) is kept in the
+// storage type, so every value is rounded exactly as in two single steps: the result equals them
+// bit for bit.  DRAM sees one read and one write of every population per two steps, plus two
+// halo rows above and below each tile that the neighbouring tiles (running at the same time)
+// mostly serve from L2.  The ring is the only shared memory: 3 x 4 x q x (128 + 8) floats,
+// 32.6 KB for D2Q5, so six blocks (24 warps) fit on an SM.
+constexpr int kTbW = 128;
 constexpr int kTbV = kTbW / 32;            // cells per lane
-constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+kTbW+3
-constexpr int kTbChunks = kTbRow / 4;      // 16-byte chunks per ring row
-constexpr int kTbR0 = 4, kTbR1 = 3;        // ring depths in 4-row blocks
+constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+131 (x0-1 .. x0+128 used)
+constexpr int kTbR1 = 3;                   // ring depth in 4-row blocks
+constexpr int kTbMinBlocks = 5;            // blocks per SM the register budget is sized for
 constexpr bool kTbPacked = true;           // collide a lane's cells as f32x2 pairs
-static_assert(kTbW == 64 || kTbW == 128, "two or four cells per lane");
+// Grids whose two population copies take at most this many bytes also ask L2 for the rows of
+// the iteration after next (prefetch.global.L2): measured on GB300 it gains 4 % on 2048^2 D2Q5
+// FP32 (168 MB, about the L2's 129 MB) and loses 6 % on 4096^2 and 4 % on 8192^2.
+constexpr long long kTbL2PrefetchMaxBytes = 256LL << 20;
 
 template <class S>
 constexpr int tb_smem_bytes() {
-    return (kTbR0 + kTbR1) * 4 * S::Q * kTbRow * (int)sizeof(float);
+    return kTbR1 * 4 * S::Q * kTbRow * (int)sizeof(float);
 }
 
-__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
-// kTbV consecutive floats of a ring row (aligned to kTbV floats) and their store.
-__device__ __forceinline__ void tb_ld(const float *p, float (&v)[kTbV]) {
-    if constexpr (kTbV == 4) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else {
-        const float2 t = *reinterpret_cast<const float2 *>(p);
-        v[0] = t.x; v[1] = t.y;
-    }
-}
 __device__ __forceinline__ void tb_st(float *p, const float (&v)[kTbV]) {
-    if constexpr (kTbV == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Pulls the kTbV cells of one lane for velocity i from a ring row (offsets relative to x0-4):
-// the lane's own cells sit at kTbV*lane+4; c_x = +1 takes one element from the left neighbour
-// lane (or offset 3 for lane 0), c_x = -1 one from the right neighbour (or offset kTbW+4 for
-// lane 31).
+// Pulls the four cells of one lane for velocity i from a ring row (offsets relative to x0-4):
+// the lane's own cells sit at 4*lane+4; c_x = +1 takes one element from the left neighbour lane
+// (or offset 3 for lane 0), c_x = -1 one from the right neighbour (or offset kTbW+4 for lane 31).
 template <int cx>
 __device__ __forceinline__ void tb_pull(const float *row, int lane, float (&out)[kTbV]) {
-    float v[kTbV];
-    tb_ld(row + kTbV * lane + 4, v);
+    const float4 t = *reinterpret_cast<const float4 *>(row + kTbV * lane + 4);
+    const float v[4] = {t.x, t.y, t.z, t.w};
     if constexpr (cx == 0) {
 #pragma unroll
         for (int e = 0; e < kTbV; ++e) out[e] = v[e];
@@ -623,112 +611,126 @@ __device__ __forceinline__ void tb_pull(const float *row, int lane, float (&out)
     }
 }
 
-// One tile (columns x0 .. x0+kTbW-1, rows y0 .. y0+H-1) of two fused steps; the whole block calls it.
-template <class S>
+// One tile (columns x0 .. x0+kTbW-1, rows y0 .. y0+H-1) of two fused steps; the whole block calls
+// it.  PF: also prefetch into L2 the rows of the iteration after next.
+template <class S, bool PF>
 __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
                                         long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
                                         float *tb_smem) {
     static_assert(S::D == 2, "two-step tiles are 2D");
     constexpr int Q = S::Q;
-    float *ring0 = tb_smem;                                // [kTbR0][4][Q][kTbRow]
-    float *ring1 = tb_smem + kTbR0 * 4 * Q * kTbRow;       // [kTbR1][4][Q][kTbRow]
-    auto r0 = [&](int blk, int w, int i) { return ring0 + (((blk % kTbR0) * 4 + w) * Q + i) * kTbRow; };
-    auto r1 = [&](int blk, int w, int i) { return ring1 + (((blk % kTbR1) * 4 + w) * Q + i) * kTbRow; };
+    auto r1 = [&](int blk, int w, int i) { return tb_smem + (((blk % kTbR1) * 4 + w) * Q + i) * kTbRow; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int iters = H / 4 + 3;
+    const int iters = H / 4 + 1;
 
-    // Block k of S(t): row y0 - 2 + 4k + warp, kTbChunks chunks of 4 columns starting at x0 - 4.
-    // Lane l copies chunk l (if l < kTbChunks) and chunk l + 32 (if that exists).  Columns wrap
-    // periodically (nx is a multiple of 4, so chunks stay 16-byte aligned; columns of the last
-    // strip past nx hold the periodic continuation of the row).  The chunk columns are fixed for
-    // the tile and the row advances by 4 per block, so both are reduced once and then stepped.
-    auto wrap_x = [&](int c) {
-        int x = (x0 - 4 + 4 * c) % nx;
+    // Periodic columns, fixed for the tile: the lane's float4 (nx is a multiple of 4, so a chunk
+    // never straddles the wrap; columns of the last strip past nx hold the periodic continuation
+    // of the row) and the scalar columns x0-2 .. x0 and x0+127 .. x0+129 of the edges.
+    auto wrap_x = [&](int x) {
+        x %= nx;
         return x < 0 ? x + nx : x;
     };
-    const bool one_chunk = lane < kTbChunks;
-    const bool two_chunks = lane + 32 < kTbChunks;
-    const int xa = one_chunk ? wrap_x(lane) : 0;
-    const int xb = two_chunks ? wrap_x(lane + 32) : 0;
-    int rcur = (y0 - 2 + warp) % ny;
-    if (rcur < 0) rcur += ny;
-    auto load_block = [&](int k) {  // called once for each k = 0, 1, 2, ... in this order
-        const int row = y0 - 2 + 4 * k + warp;
-        if (row <= y0 + H + 1) {
-            const float *rp = src + (long long)rcur * nx;
-            float *sp = r0(k, warp, 0);
-            if (one_chunk) {
+    const int xa = wrap_x(x0 + kTbV * lane);
+    int xe[6];  // columns x0-2, x0-1, x0, x0+127, x0+128, x0+129
 #pragma unroll
-                for (int i = 0; i < Q; ++i) cp_async_16(sp + i * kTbRow + 4 * lane, rp + (long long)i * pitch + xa);
-            }
-            if (two_chunks) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    cp_async_16(sp + i * kTbRow + 4 * (lane + 32), rp + (long long)i * pitch + xb);
+    for (int e = 0; e < 3; ++e) {
+        xe[e] = wrap_x(x0 - 2 + e);
+        xe[3 + e] = wrap_x(x0 + kTbW - 1 + e);
+    }
+    // Loads of pass A are issued one iteration ahead into registers, so their latency overlaps
+    // the barrier and pass B of the iteration before.  Row a = y0 - 1 + 4k + warp of S(t+1) needs
+    // S(t) rows a-1, a, a+1; rn is row a of the next iteration to load, reduced modulo ny.
+    struct Pre {
+        float4 t[Q];      // the lane's four cells of velocity i from row a - c_y
+        float edge[Q];    // lane 0: column x0-1 (c_x = +1); lane 31: column x0+128 (c_x = -1)
+        float halo[Q][2]; // lane 0: the pulls of the halo columns x0-1 and x0+128
+    };
+    Pre pre;
+    int rn = (y0 - 1 + warp) % ny;
+    if (rn < 0) rn += ny;
+    auto load_a = [&](int k) {  // called once for each k = 0, 1, 2, ... in this order
+        const int a = y0 - 1 + 4 * k + warp;
+        if (a <= y0 + H) {
+            const int rows[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};  // a-1, a, a+1
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                const float *rowp = src + (long long)i * pitch + (long long)rows[1 - cy] * nx;
+                pre.t[i] = __ldg(reinterpret_cast<const float4 *>(rowp + xa));
+                if constexpr (cx == 1) {
+                    if (lane == 0) pre.edge[i] = __ldg(rowp + xe[1]);
+                } else if constexpr (cx == -1) {
+                    if (lane == 31) pre.edge[i] = __ldg(rowp + xe[4]);
+                }
+                if (lane == 0) {  // cell x pulls velocity i from column x - c_x
+                    pre.halo[i][0] = __ldg(rowp + xe[1 - cx]);
+                    pre.halo[i][1] = __ldg(rowp + xe[4 - cx]);
+                }
+            });
+        }
+        rn += 4;
+        while (rn >= ny) rn -= ny;  // at most two passes: ny >= 3
+        if constexpr (PF) {
+            // one lane per 128-byte line of the warp's 512 bytes, only for rows the tile needs
+            if ((lane & 7) == 0 && a + 4 <= y0 + H) {
+                const int rows2[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cy = S::c(i, 1);
+                    prefetch_l2(src + (long long)i * pitch + (long long)rows2[1 - cy] * nx + xa);
+                });
             }
         }
-        cp_async_commit();  // one group per block (empty when nothing is needed)
-        rcur += 4;
-        while (rcur >= ny) rcur -= ny;  // at most two passes: ny >= 3
     };
+    load_a(0);
+
+    // B_k: S(t+2) row b from S(t+1) rows b-1 .. b+1 of the ring, collided and stored.
+    auto pass_b = [&](int b) {
+        float pb[Q][kTbV];
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+            const int rr = b - cy - (y0 - 1);  // row within the S(t+1) blocks
+            tb_pull<cx>(r1(rr >> 2, rr & 3, i), lane, pb[i]);
+        });
+        float post[Q][kTbV];
+        collide_chunk<S, kTbPacked>(pb, post, cf);
+        if (b < ny && x0 + kTbV * lane < nx) {
+            float *outp = dst + (long long)b * nx + x0 + kTbV * lane;
 #pragma unroll
-    for (int k = 0; k < kTbPrefetch; ++k) load_block(k);
+            for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
+        }
+    };
 
     for (int k = 0; k < iters; ++k) {
-        cp_async_wait<kTbPrefetch - 1>();
-        __syncthreads();  // L_k complete and visible; A_{k-1} complete (read by B_k)
-        load_block(k + kTbPrefetch);  // ring slot (k+2) % 4: neither L_{k-1} nor L_k
-        // A_k: S(t+1) row a = y0 + 4k - 5 + warp (rows past y0 + H are not needed);
-        // B_k: S(t+2) row b = y0 + 4k - 12 + warp from A_{k-2}, A_{k-1}.  Both pulls are issued
-        // before either collision so that each warp has two independent streams of work.
-        const int a = y0 + 4 * k - 5 + warp;
-        const int b = y0 + 4 * k - 12 + warp;
-        const bool doA = k >= 1 && a <= y0 + H;  // warp-uniform
-        const bool doB = k >= 3 && b < y0 + H;
-        float pa[Q][kTbV], pb[Q][kTbV];
-        if (doB) {
+        const int a = y0 - 1 + 4 * k + warp;
+        if (a <= y0 + H) {  // warp-uniform; rows past y0 + H are not needed
+            float pa[Q][kTbV];
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                const int rr = b - cy - (y0 - 5);  // row within the S(t+1) blocks
-                tb_pull<cx>(r1(rr >> 2, rr & 3, i), lane, pb[i]);
+                constexpr int cx = S::c(i, 0);
+                const float4 t = pre.t[i];
+                if constexpr (cx == 0) {
+                    pa[i][0] = t.x; pa[i][1] = t.y; pa[i][2] = t.z; pa[i][3] = t.w;
+                } else if constexpr (cx == 1) {
+                    float left = __shfl_up_sync(kFull, t.w, 1);
+                    if (lane == 0) left = pre.edge[i];
+                    pa[i][0] = left; pa[i][1] = t.x; pa[i][2] = t.y; pa[i][3] = t.z;
+                } else {
+                    float right = __shfl_down_sync(kFull, t.x, 1);
+                    if (lane == 31) right = pre.edge[i];
+                    pa[i][0] = t.y; pa[i][1] = t.z; pa[i][2] = t.w; pa[i][3] = right;
+                }
             });
-        }
-        if (doA) {
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                const int rr = a - cy - (y0 - 2);  // row within the S(t) blocks
-                tb_pull<cx>(r0(rr >> 2, rr & 3, i), lane, pa[i]);
-            });
-        }
-        if (doB) {
-            float post[Q][kTbV];
-            collide_chunk<S, kTbPacked>(pb, post, cf);
-            if (b < ny && x0 + kTbV * lane < nx) {
-                float *outp = dst + (long long)b * nx + x0 + kTbV * lane;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
-            }
-        }
-        if (doA) {
             float post[Q][kTbV];
             collide_chunk<S, kTbPacked>(pa, post, cf);
 #pragma unroll
             for (int i = 0; i < Q; ++i) tb_st(r1(k, warp, i) + kTbV * lane + 4, post[i]);
-            // the two halo columns of S(t+1), x0 - 1 (offset 3) and x0 + kTbW (offset kTbW + 4),
-            // as one pair in lane 0
+            // the two halo columns of S(t+1), x0 - 1 (offset 3) and x0 + 128 (offset kTbW + 4), as
+            // one pair in lane 0
             if (lane == 0) {
-                float p1[Q][2], q1[Q][2];
-                static_for<Q>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                    const int rr = a - cy - (y0 - 2);
-                    const float *row = r0(rr >> 2, rr & 3, i);
-                    p1[i][0] = row[3 - cx];
-                    p1[i][1] = row[kTbW + 4 - cx];
-                });
-                collide_chunk<S, kTbPacked>(p1, q1, cf);
+                float q1[Q][2];
+                collide_chunk<S, kTbPacked>(pre.halo, q1, cf);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     r1(k, warp, i)[3] = q1[i][0];
@@ -736,16 +738,20 @@ __device__ __forceinline__ void tb_tile(const float *__restrict__ src, float *__
                 }
             }
         }
+        if (k + 1 < iters) load_a(k + 1);
+        __syncthreads();  // A_k complete and visible; every B_{k-1} done (slot k+1 is free)
+        // B_k: rows y0 + 4k - 4 .. y0 + 4k - 1 from slots k-1, k
+        if (k >= 1) pass_b(y0 + 4 * k - 4 + warp);
     }
-    cp_async_wait<0>();
 }
 
-template <class S>
-__global__ void __launch_bounds__(128) k_stream_collide_2step(const float *__restrict__ src, float *__restrict__ dst,
-                                                              int nx, int ny, long long pitch, int H,
-                                                              CollideCoef<float> cf) {
+template <class S, bool PF>
+__global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step(const float *__restrict__ src,
+                                                                            float *__restrict__ dst, int nx, int ny,
+                                                                            long long pitch, int H,
+                                                                            CollideCoef<float> cf) {
     extern __shared__ __align__(16) float tb_smem[];
-    tb_tile<S>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
+    tb_tile<S, PF>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
 }
 
 // Two fused steps over many periodic domains.  Block b works on tile tiles[b] = (domain,
@@ -758,14 +764,14 @@ struct TbDomain {
 };
 
 template <class S>
-__global__ void __launch_bounds__(128) k_stream_collide_2step_batched(const float *__restrict__ src,
+__global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batched(const float *__restrict__ src,
                                                                       float *__restrict__ dst,
                                                                       const TbDomain *__restrict__ doms,
                                                                       const int3 *__restrict__ tiles) {
     extern __shared__ __align__(16) float tb_smem[];
     const int3 tl = tiles[blockIdx.x];
     const TbDomain &D = doms[tl.x];
-    tb_tile<S>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
+    tb_tile<S, false>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
 }
 
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the

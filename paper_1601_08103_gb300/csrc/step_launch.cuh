@@ -78,10 +78,15 @@ cudaError_t two_step_prepare() {
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
         if (two_step_capacity<S>()[dev]) return cudaSuccess;
         constexpr int smem = tb_smem_bytes<S>();
-        e = cudaFuncSetAttribute(k_stream_collide_2step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_stream_collide_2step<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stream_collide_2step<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step<S>, 128, smem);
+        int per_sm = 0, per_sm_pf = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step<S, false>, 128, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pf, k_stream_collide_2step<S, true>, 128, smem);
+        if (per_sm_pf < per_sm) per_sm = per_sm_pf;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         two_step_capacity<S>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
@@ -108,9 +113,10 @@ cudaError_t two_step_launch(const StepLaunch &L) {
         H = (H + 3) / 4 * 4;
         if (H < 16) H = 16;
         const dim3 grid(strips, (L.ny + H - 1) / H);
-        k_stream_collide_2step<S><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
-                                                                 static_cast<float *>(L.dst), L.nx, L.ny, L.pitch, H,
-                                                                 cf);
+        const long long bytes = 2LL * S::Q * (long long)sizeof(float) * L.nx * L.ny;
+        auto kern = bytes <= kTbL2PrefetchMaxBytes ? k_stream_collide_2step<S, true> : k_stream_collide_2step<S, false>;
+        kern<<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src), static_cast<float *>(L.dst), L.nx, L.ny,
+                                            L.pitch, H, cf);
         return cudaGetLastError();
     }
 }
