@@ -415,6 +415,33 @@ def forms_configs():
     return out
 
 
+def forms_stability():
+    """The von Neumann scan of Theorem 1 (Sec. 7) on the GPU: grid points per second and the
+    extreme values of the spectral radius and kappa_W, for tau = 1/2 and 0.7."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+
+    out = {}
+    for name, m in (("D2Q5", 512), ("D3Q7_DI", 48), ("D3Q19", 48)):
+        info = lee.lee_velset_info(name)
+        n = m ** info["D"]
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        kap = torch.empty(n, dtype=torch.float64, device="cuda")
+        nu = torch.empty(n, dtype=torch.float64, device="cuda")
+        for tau in (0.5, 0.7):
+            lee.lee_stability_scan(name, tau, m, rho, None, kap, nu)  # warm-up (local memory set-up)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lee.lee_stability_scan(name, tau, m, rho, None, kap, nu)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[f"{name}_m{m}_tau{tau}"] = {"points": n, "s": round(dt, 4), "points_per_s": round(n / dt, 1),
+                                            "rho_max": float(rho.max()), "kappa_max": float(kap.max()),
+                                            "nu_max": float(nu.max())}
+    return out
+
+
 def forms_batched(steps: int = 1000):
     """Batched 2D form: 96 periodic D2Q5 domains (sizes from {128, ..., 1024}^2, tau in
     [0.52, 1.2], one pulse each, seed 4), FP32, `steps` steps, in one batched launch per step
@@ -597,6 +624,7 @@ def main(argv=None):
         if world == 1 and not args.no_forms:
             line["forms"] = forms_3d()
             line["forms_configs"] = forms_configs()
+            line["forms_stability"] = forms_stability()
             line["forms_batched"] = forms_batched()
             line["forms_learned"] = forms_learned()
         print(json.dumps(line), flush=True)

@@ -65,6 +65,7 @@ _SIGS = {
     "lee_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lee_velset_info": (ctypes.c_int, [_I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P, _P, _P, _P]),
     "lee_units_from_dimensional": (ctypes.c_int, [_I32, _D, _D, _D, _D, _I64, _D, ctypes.POINTER(lee_units)]),
+    "lee_stability_scan": (ctypes.c_int, [_I32, _D, _I32, _D, _P, _P, _P, _P, _P]),
     "lee_lbm_create": (ctypes.c_int, [ctypes.POINTER(lee_lbm_config), ctypes.POINTER(_P)]),
     "lee_lbm_init_fields": (ctypes.c_int, [_P, _P, _P, _P, _I32]),
     "lee_lbm_step": (ctypes.c_int, [_P, _I64]),
@@ -304,6 +305,22 @@ def lee_reduce_noalloc(set_name: str, storage: str, g, cells: int, pitch: int, o
     st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
     _check(lib.lee_reduce_noalloc(SETS[set_name], STORAGE[storage], ga, int(cells), int(pitch), float(store_scale), oa,
                                   st), "lee_reduce_noalloc")
+
+
+def lee_stability_scan(set_name: str, tau: float, m: int, rho, lam=None, kappa=None, nu=None, delta: float = 1e-6,
+                       stream=None):
+    """Von Neumann scan of Gamma(k) = D(k) H(tau) on the m^D grid of wave vectors (see
+    include/lee_stability.h).  rho [m^D], and optionally lam [m^D][q][2], kappa [m^D], nu [m^D]:
+    CUDA float64 tensors, filled on `stream` (the call waits for it)."""
+    lib = load()
+    bufs = [rho, lam, kappa, nu]
+    for b in bufs:
+        if b is not None and not _addr(b)[1]:
+            raise ValueError("lee_stability_scan takes device buffers only")
+    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
+    ra, la, ka, na = (_addr(b)[0] for b in bufs)
+    _check(lib.lee_stability_scan(SETS[set_name], float(tau), int(m), float(delta), la, ra, ka, na, st),
+           "lee_stability_scan")
 
 
 class Solver:

@@ -102,3 +102,12 @@ def test_null_handle_and_destroy_are_safe(lib):
 def test_binding_rejects_mixed_host_and_device_buffers():
     a = np.zeros(4)
     assert lee._same_place(a, None, a) == 0
+
+
+def test_stability_scan_rejects_bad_arguments_on_the_host(lib):
+    """Validation happens before any device work, so it runs without a GPU."""
+    raw = lee.load()
+    assert raw.lee_stability_scan(0, 0.5, 8, 1e-6, None, None, None, None, None) == lee.LEE_ERR_INVALID_ARGUMENT  # rho NULL
+    fake = 16  # never dereferenced: every call below fails validation first
+    for args in [(0, -1.0, 8, 1e-6), (0, 0.5, 0, 1e-6), (0, 0.5, 8, 0.0), (42, 0.5, 8, 1e-6), (6, 0.5, 300, 1e-6)]:
+        assert raw.lee_stability_scan(*args, None, fake, None, None, None) == lee.LEE_ERR_INVALID_ARGUMENT, args
