@@ -517,6 +517,10 @@ CASES = {
     "d3q7_f16": ("D3Q7", (384, 384, 384), "f16", 0.55),
     "d3q7_bf16": ("D3Q7", (384, 384, 384), "bf16", 0.55),
     "d3q19_f32": ("D3Q19", (256, 256, 256), "f32", 0.55),
+    "d3q19_f16": ("D3Q19", (256, 256, 256), "f16", 0.55),
+    "d3q19_split16": ("D3Q19", (256, 256, 256), "split16", 0.55),
+    "d3q13_f32": ("D3Q13", (256, 256, 256), "f32", 0.55),
+    "d3q13_split16": ("D3Q13", (256, 256, 256), "split16", 0.55),
     "d2q5_f32_4096": ("D2Q5", (4096, 4096, 1), "f32", 0.6),
     "d2q5_f32_8192": ("D2Q5", (8192, 8192, 1), "f32", 0.6),
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
@@ -559,7 +563,7 @@ def run_case(args):
         ms = e0.elapsed_time(e1)
         ok = sv.check_finite()
     q = lee.lee_velset_info(name)["q"]
-    bpl = 2 * q * lee.STORAGE_BYTES[storage]
+    bpl = 2 * lee.state_bytes_per_cell(D, q, storage)
     print(json.dumps({"case": args.case, "cells": cells, "steps": args.steps, "ms": ms, "finite": ok,
                       "mlups": cells * args.steps / (ms / 1e3) / 1e6,
                       "gbs": bpl * cells * args.steps / (ms / 1e3) / 1e9}), flush=True)

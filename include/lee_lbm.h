@@ -79,8 +79,18 @@ typedef enum { LEE_BC_PERIODIC = 0, LEE_BC_OPEN_ZERO = 1, LEE_BC_OPEN_SPONGE = 2
 /* Storage of the populations in device memory.  Collision arithmetic is FP64 for F64 storage and
  * FP32 otherwise.  The 16-bit forms store S * g_i / f*_i rounded to nearest-even, with S a power
  * of two (config.store_scale, or chosen by init_fields when 0) -- g is already the deviation from
- * the rest state, since F = M (1 + epsilon g) (Sec. 3). */
-typedef enum { LEE_STORE_F64 = 0, LEE_STORE_F32 = 1, LEE_STORE_F16 = 2, LEE_STORE_BF16 = 3 } lee_storage;
+ * the rest state, since F = M (1 + epsilon g) (Sec. 3).
+ * SPLIT16 (periodic grids only) keeps per cell the conserved moments (rho', j, E) in FP32 and the
+ * post-collision non-equilibrium parts n*_i = (1 - 1/tau) (g_i - g_i^eq) in FP16 as S n*_i / f*_i:
+ * 4 (D + 2) + 2 q bytes per cell and copy (58 B for D3Q19 against 76 B in FP32), with only the
+ * small non-equilibrium part rounded to 16 bits.  It pays for the q-heavy sets (D3Q19, D3Q13). */
+typedef enum {
+    LEE_STORE_F64 = 0,
+    LEE_STORE_F32 = 1,
+    LEE_STORE_F16 = 2,
+    LEE_STORE_BF16 = 3,
+    LEE_STORE_SPLIT16 = 4
+} lee_storage;
 
 typedef struct {
     int32_t set;            /* lee_velset                                                   */

@@ -17,9 +17,17 @@ LIB_PATH = _build.LIB
 
 # enums of include/lee_lbm.h
 SETS = {"D1Q3": 0, "D2Q5": 1, "D2Q5_DI": 2, "D3Q7": 3, "D3Q9": 4, "D3Q13": 5, "D3Q19": 6, "D3Q7_DI": 7}
-STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "split16": 4}
 BC = {"periodic": 0, "open_zero": 1, "open_sponge": 2, "open_learned": 3}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def state_bytes_per_cell(D: int, q: int, storage: str) -> int:
+    """Bytes of one cell in one state copy: q populations, or for split16 the D + 2 FP32 moments
+    and q FP16 non-equilibrium parts."""
+    if storage == "split16":
+        return 4 * (D + 2) + 2 * q
+    return q * STORAGE_BYTES[storage]
 
 LEE_OK = 0
 LEE_ERR_INVALID_ARGUMENT = 1

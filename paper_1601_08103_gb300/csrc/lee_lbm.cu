@@ -10,6 +10,7 @@
 
 #include "../../include/lee_lbm.h"
 #include "handles.cuh"
+#include "split.cuh"
 
 // fold_coefficients evaluates host-side constants in long double; the device pass of nvcc notes
 // that long double would be double there, which does not apply to this host-only code.
@@ -152,8 +153,20 @@ size_t elem_size(int storage) {
     case LEE_STORE_F32: return 4;
     case LEE_STORE_F16:
     case LEE_STORE_BF16: return 2;
+    case LEE_STORE_SPLIT16: return 2;  // the non-equilibrium arrays; the moments come on top
     default: return 0;
     }
+}
+
+// Bytes of one state copy.
+size_t state_bytes(int storage, int D, int Q, long long pitch) {
+    if (storage == LEE_STORE_SPLIT16) return (size_t)split_bytes_per_cell(D, Q) * (size_t)pitch;
+    return elem_size(storage) * (size_t)Q * (size_t)pitch;
+}
+
+// 16-bit forms whose storage scale S is chosen from the initial fields.
+bool scaled_storage(int storage) {
+    return storage == LEE_STORE_F16 || storage == LEE_STORE_BF16 || storage == LEE_STORE_SPLIT16;
 }
 
 void free_all(lee_lbm *h) {
@@ -268,6 +281,7 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     }
     if (cfg->bc == LEE_BC_OPEN_LEARNED && !(o->D == 2 && o->Q == 5)) return LEE_ERR_UNSUPPORTED;
     if (cfg->bc == LEE_BC_OPEN_LEARNED && (cfg->nx < 3 || cfg->ny < 3)) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->storage == LEE_STORE_SPLIT16 && cfg->bc != LEE_BC_PERIODIC) return LEE_ERR_UNSUPPORTED;
     if (cfg->store_scale < 0.0 || !std::isfinite(cfg->store_scale)) return LEE_ERR_INVALID_ARGUMENT;
     if (cfg->store_scale > 0.0) {
         int ex = 0;
@@ -287,10 +301,9 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (const char *ev = std::getenv("LEE_SINGLE_STEP")) h->single_step_only = ev[0] == '1';
     if (const char *ev = std::getenv("LEE_FORCE_SCALAR")) h->force_scalar = ev[0] == '1';
     if (h->force_scalar) h->single_step_only = true;
-    const bool is16 = cfg->storage == LEE_STORE_F16 || cfg->storage == LEE_STORE_BF16;
-    h->scale = is16 ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
+    h->scale = scaled_storage(cfg->storage) ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
-    const size_t bytes = h->elem * (size_t)h->Q * (size_t)h->pitch;
+    const size_t bytes = state_bytes(cfg->storage, h->D, h->Q, h->pitch);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], bytes);
     h->nblocks = aux_blocks(cells, kReduceThreads);
@@ -333,8 +346,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
         du = fu;
         dt = ft;
     }
-    const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
-    if (is16 && h->cfg.store_scale == 0.0) {
+    if (scaled_storage(h->cfg.storage) && h->cfg.store_scale == 0.0) {
         LEE_CK(h, cudaMemsetAsync(h->maxbits, 0, sizeof(unsigned int), h->st), "memset maxbits");
         LEE_CK(h, h->ops->init_maxabs(dr, du, dt, h->cells, consts_for(h->cfg.set, 1.0), h->maxbits, h->st), "init_maxabs");
         unsigned int bits = 0;
@@ -383,6 +395,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.ghost = learned ? h->ghost : nullptr;
     L.ghost_L = learned ? h->ghost_L : 0;
     L.force_scalar = h->force_scalar ? 1 : 0;
+    L.store_scale = h->scale;
     // One time step's launches (boundary network first for the learned edge) on stream `st`.
     auto launch_step = [&](int from, cudaStream_t st) -> cudaError_t {
         L.src = h->buf[from];
@@ -397,7 +410,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     };
     int64_t left = n;
     // 1D grids that fit in shared memory: every step in one launch of the on-chip kernel
-    if (h->ops->onchip_1d && n >= 2 &&
+    if (h->ops->onchip_1d && n >= 2 && h->cfg.storage != LEE_STORE_SPLIT16 &&
         2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem) {
         L.stream = h->st;
         LEE_CK(h, h->ops->onchip_1d(L, h->buf[h->cur], n), "on-chip 1D launch");
@@ -573,7 +586,8 @@ lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
     const bool two = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
                      h->cfg.nx % 4 == 0 && h->cfg.ny >= 3 && !h->single_step_only;
-    const bool onchip = h->ops->onchip_1d && 2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
+    const bool onchip = h->ops->onchip_1d && h->cfg.storage != LEE_STORE_SPLIT16 &&
+                        2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
     *steps = onchip ? 0 : (two ? 2 : 1);
     return LEE_OK;
 }

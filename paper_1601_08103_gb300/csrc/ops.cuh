@@ -26,6 +26,7 @@ struct StepLaunch {
     const void *ghost;   // float (or double for F64) [4][ghost_L], or nullptr
     int ghost_L;
     int force_scalar;    // 1: use the one-cell-per-thread variant (testing)
+    double store_scale;  // storage scale S of the 16-bit and split forms (1 otherwise)
     cudaStream_t stream;
 };
 

@@ -1,13 +1,68 @@
 // set_impl.cuh -- host launchers for one velocity set, instantiated by the set_*.cu units.
 #pragma once
 
+#include "split.cuh"
 #include "step_launch.cuh"
 
 namespace lee {
 
+// Split storage (split.cuh): pointers into one state copy and the FP32 coefficients.
+template <class S>
+struct SplitView {
+    static float *m(void *base) { return static_cast<float *>(base); }
+    static const float *m(const void *base) { return static_cast<const float *>(base); }
+    static __half *n(void *base, long long pitch) {
+        return reinterpret_cast<__half *>(static_cast<float *>(base) + (long long)(S::D + 2) * pitch);
+    }
+    static const __half *n(const void *base, long long pitch) {
+        return reinterpret_cast<const __half *>(static_cast<const float *>(base) + (long long)(S::D + 2) * pitch);
+    }
+};
+
+template <class S>
+SplitCoef split_coef(double omega, double scale) {
+    const SetConsts k = host_consts<S>(scale);
+    SplitCoef c{};
+    for (int t = 0; t < 4; ++t) {
+        const double fa = k.a1 + 0.5 * t * k.c1, fb = k.a2 + 0.5 * t * k.c2;
+        c.alpha[t] = (float)(k.f[t] * (fa - k.kR * fb));
+        c.beta[t] = (float)(k.f[t] * k.kE * fb);
+        c.gamma[t] = (float)(k.f[t] * k.b * k.inv_rho0);
+        c.ew[t] = (float)k.ew[t];
+        c.dec[t] = (float)k.dec[t];
+        c.enc[t] = (float)k.enc[t];
+    }
+    c.one_minus_omega = 1.0f - (float)omega;
+    return c;
+}
+
+template <class S>
+cudaError_t launch_split_step(const StepLaunch &L) {
+    if (L.open) return cudaErrorInvalidValue;  // periodic grids only
+    constexpr int VV = S::Q > 13 ? 2 : 4;  // bound the registers of the q-heavy sets
+    const int V = (L.force_scalar || L.nx % VV != 0) ? 1 : VV;
+    GridDesc gd;
+    gd.nx = L.nx;
+    gd.ny = L.ny;
+    gd.nz = L.nz;
+    gd.nxc = L.nx / V;
+    gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
+    gd.pitch = L.pitch;
+    const SplitCoef cf = split_coef<S>(L.omega, L.store_scale);
+    const unsigned blocks = (unsigned)((gd.nchunks + 127) / 128);
+    const float *ms = SplitView<S>::m(L.src);
+    const __half *ns = SplitView<S>::n(L.src, L.pitch);
+    float *md = SplitView<S>::m(L.dst);
+    __half *nd = SplitView<S>::n(L.dst, L.pitch);
+    if (V == VV) k_split_step<S, VV><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
+    else k_split_step<S, 1><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
+    return cudaGetLastError();
+}
+
 template <class S>
 struct SetImpl {
     static cudaError_t step(const StepLaunch &L) {
+        if (L.storage == LEE_STORE_SPLIT16) return launch_split_step<S>(L);
         return with_storage(L.storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             return launch_step_t<S, T>(L);
@@ -15,6 +70,11 @@ struct SetImpl {
     }
     static cudaError_t init(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                             long long pitch, const SetConsts &k, cudaStream_t st) {
+        if (storage == LEE_STORE_SPLIT16) {
+            k_split_init<S><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, SplitView<S>::m(g),
+                                                               SplitView<S>::n(g, pitch), cells, pitch, k);
+            return cudaGetLastError();
+        }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             k_init_equilibrium<S, T><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, static_cast<T *>(g), cells, pitch, k);
@@ -28,6 +88,10 @@ struct SetImpl {
     }
     static cudaError_t moments(int storage, const void *g, long long cells, long long pitch, const SetConsts &k, double *rho,
                                double *u, double *theta, cudaStream_t st) {
+        if (storage == LEE_STORE_SPLIT16) {
+            k_split_moments<S><<<aux_blocks(cells), 256, 0, st>>>(SplitView<S>::m(g), cells, pitch, k, rho, u, theta);
+            return cudaGetLastError();
+        }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             k_moments<S, T><<<aux_blocks(cells), 256, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, rho, u, theta);
@@ -36,6 +100,11 @@ struct SetImpl {
     }
     static cudaError_t reduce_partial(int storage, const void *g, long long cells, long long pitch, const SetConsts &k,
                                       double *partial, int nblocks, cudaStream_t st) {
+        if (storage == LEE_STORE_SPLIT16) {
+            k_split_reduce_partial<S><<<nblocks, kReduceThreads, 0, st>>>(SplitView<S>::m(g), SplitView<S>::n(g, pitch),
+                                                                          cells, pitch, k, partial);
+            return cudaGetLastError();
+        }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             k_reduce_partial<S, T><<<nblocks, kReduceThreads, 0, st>>>(static_cast<const T *>(g), cells, pitch, partial);
@@ -44,6 +113,11 @@ struct SetImpl {
     }
     static cudaError_t export_f64(int storage, const void *g, long long cells, long long pitch, const SetConsts &k,
                                   double *out, cudaStream_t st) {
+        if (storage == LEE_STORE_SPLIT16) {
+            k_split_export<S><<<aux_blocks(cells), 256, 0, st>>>(SplitView<S>::m(g), SplitView<S>::n(g, pitch), cells,
+                                                                 pitch, k, out);
+            return cudaGetLastError();
+        }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             k_export<S, T><<<aux_blocks(cells), 256, 0, st>>>(static_cast<const T *>(g), cells, pitch, k, out);
@@ -52,6 +126,11 @@ struct SetImpl {
     }
     static cudaError_t import_f64(int storage, const double *in, long long cells, long long pitch, const SetConsts &k,
                                   void *g, cudaStream_t st) {
+        if (storage == LEE_STORE_SPLIT16) {
+            k_split_import<S><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, k, SplitView<S>::m(g),
+                                                                 SplitView<S>::n(g, pitch));
+            return cudaGetLastError();
+        }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
             k_import<S, T><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, k, static_cast<T *>(g));

@@ -83,6 +83,8 @@ def test_velset_info_matches_paper_tables(lib):
     (dict(bc="open_sponge", sponge_width=4, shape=(8, 64, 1)), lee.LEE_ERR_INVALID_ARGUMENT),  # frame too wide
     (dict(store_scale=3.0), lee.LEE_ERR_INVALID_ARGUMENT),       # not a power of two
     (dict(set_name="D3Q7", shape=(8, 8, 8), bc="open_learned"), lee.LEE_ERR_UNSUPPORTED),
+    (dict(set_name="D3Q19", shape=(8, 8, 8), storage="split16", bc="open_zero"), lee.LEE_ERR_UNSUPPORTED),
+    (dict(storage="split16", bc="open_sponge", sponge_width=2), lee.LEE_ERR_UNSUPPORTED),
 ])
 def test_create_rejects_bad_configs_on_the_host(lib, kw, status):
     args = dict(set_name="D2Q5", shape=(16, 8, 1), tau=0.6)
