@@ -49,13 +49,18 @@ cudaError_t launch_split_step(const StepLaunch &L) {
     gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
     gd.pitch = L.pitch;
     const SplitCoef cf = split_coef<S>(L.omega, L.store_scale);
-    const unsigned blocks = (unsigned)((gd.nchunks + 127) / 128);
     const float *ms = SplitView<S>::m(L.src);
     const __half *ns = SplitView<S>::n(L.src, L.pitch);
     float *md = SplitView<S>::m(L.dst);
     __half *nd = SplitView<S>::n(L.dst, L.pitch);
-    if (V == VV) k_split_step<S, VV><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
-    else k_split_step<S, 1><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
+    if (V == VV && gd.nxc % 32 == 0) {
+        const long long tiles = (long long)(gd.nxc / 32) * ((L.ny + 3) / 4) * L.nz;
+        k_split_step<S, VV, true><<<(unsigned)tiles, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
+        return cudaGetLastError();
+    }
+    const unsigned blocks = (unsigned)((gd.nchunks + 127) / 128);
+    if (V == VV) k_split_step<S, VV, false><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
+    else k_split_step<S, 1, false><<<blocks, 128, 0, L.stream>>>(ms, ns, md, nd, gd, cf);
     return cudaGetLastError();
 }
 

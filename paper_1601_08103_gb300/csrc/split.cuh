@@ -58,18 +58,35 @@ __host__ __device__ constexpr int first_of_row(int i) {
 // One step: every thread V consecutive cells of an x-row; all lanes of a warp take part in the
 // shuffles (lanes past the end work on a clamped chunk and store nothing).  The moments of each
 // source row (c_y, c_z) are loaded once and serve every velocity that pulls from that row.
-template <class S, int V>
+// TILED (nx a multiple of 32 V): the 4 warps of a block take the same 32 V columns of 4
+// consecutive y-rows of one z-plane, so the moment rows y-1 .. y+4 they pull from are shared in
+// L1; otherwise threads take consecutive chunks of the grid in x, y, z order.
+template <class S, int V, bool TILED>
 __global__ void __launch_bounds__(128, 4) k_split_step(const float *__restrict__ msrc, const __half *__restrict__ nsrc,
-                                                    float *__restrict__ mdst, __half *__restrict__ ndst, GridDesc gd,
-                                                    SplitCoef cf) {
+                                                       float *__restrict__ mdst, __half *__restrict__ ndst, GridDesc gd,
+                                                       SplitCoef cf) {
     constexpr int Q = S::Q, D = S::D, NM = D + 2;
-    const long long raw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = raw < gd.nchunks;
-    const long long chunk = active ? raw : gd.nchunks - 1;
     const int lane = threadIdx.x & 31;
-    const int xc = (int)(chunk % gd.nxc);
-    const long long row = chunk / gd.nxc;
-    const int y = (int)(row % gd.ny), z = (int)(row / gd.ny);
+    bool active;
+    int xc, y, z;
+    if constexpr (TILED) {
+        const int nbx = gd.nxc / 32, nby = (gd.ny + 3) / 4;
+        const long long b = blockIdx.x;
+        xc = (int)(b % nbx) * 32 + lane;
+        const long long t = b / nbx;
+        y = (int)(t % nby) * 4 + (threadIdx.x >> 5);
+        z = (int)(t / nby);
+        if (y >= gd.ny) return;  // the whole warp: no shuffle partner is left behind
+        active = true;
+    } else {
+        const long long raw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        active = raw < gd.nchunks;
+        const long long chunk = active ? raw : gd.nchunks - 1;
+        xc = (int)(chunk % gd.nxc);
+        const long long row = chunk / gd.nxc;
+        y = (int)(row % gd.ny);
+        z = (int)(row / gd.ny);
+    }
     const int x0 = xc * V;
     const bool has_left = lane > 0 && xc > 0, has_right = lane < 31 && xc < gd.nxc - 1;
 
