@@ -62,7 +62,7 @@ __host__ __device__ constexpr int first_of_row(int i) {
 // consecutive y-rows of one z-plane, so the moment rows y-1 .. y+4 they pull from are shared in
 // L1; otherwise threads take consecutive chunks of the grid in x, y, z order.
 template <class S, int V, bool TILED>
-__global__ void __launch_bounds__(128, 4) k_split_step(const float *__restrict__ msrc, const __half *__restrict__ nsrc,
+__global__ void __launch_bounds__(128, 5) k_split_step(const float *__restrict__ msrc, const __half *__restrict__ nsrc,
                                                        float *__restrict__ mdst, __half *__restrict__ ndst, GridDesc gd,
                                                        SplitCoef cf) {
     constexpr int Q = S::Q, D = S::D, NM = D + 2;
