@@ -442,6 +442,46 @@ def forms_stability():
     return out
 
 
+def forms_split():
+    """Split storage on the velocity set it is for: D3Q19 256^3, tau = 0.55, Gaussian pulse
+    (A = 1e-3, w = 16), 200 steps, in FP32, FP16 and split16 (FP32 moments + FP16 non-equilibrium
+    parts): MLUPS, algorithmic GB/s, bytes per cell and copy, and the relative L2 error of rho'
+    against the FP64 run on the same GPU."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+
+    name, n, steps = "D3Q19", 256, 200
+    info = lee.lee_velset_info(name)
+    cells = n ** 3
+    stream = torch.cuda.current_stream()
+    rho = _device_pulse((n, n, n), 1e-3, 16.0, [n / 2.7] * 3)
+    u = torch.zeros((3, cells), dtype=torch.float64, device="cuda")
+    th = torch.zeros(cells, dtype=torch.float64, device="cuda")
+    out, ref = {}, None
+    for storage in ("f64", "f32", "f16", "split16"):
+        with lee.Solver(name, (n, n, n), 0.55, storage=storage, stream=stream) as sv:
+            sv.init_fields(rho, u, th)
+            sv.step(2)
+            sv.init_fields(rho, u, th)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sv.step(steps)
+            e1.record(stream)
+            r = torch.empty(cells, dtype=torch.float64, device="cuda")
+            sv.moments(r, None, None)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        if ref is None:
+            ref = r
+        bpc = lee.state_bytes_per_cell(3, info["q"], storage)
+        out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
+                        "gbs": round(2 * bpc * cells * steps / (ms / 1e3) / 1e9, 1), "bytes_per_cell_copy": bpc,
+                        "rel_l2_rho_vs_f64": float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))}
+    return {"workload": "3D D3Q19 periodic 256^3, tau=0.55, pulse A=1e-3 w=16, 200 steps", "storage": out}
+
+
 def forms_batched(steps: int = 1000):
     """Batched 2D form: 96 periodic D2Q5 domains (sizes from {128, ..., 1024}^2, tau in
     [0.52, 1.2], one pulse each, seed 4), FP32, `steps` steps, in one batched launch per step
@@ -629,6 +669,7 @@ def main(argv=None):
             line["forms"] = forms_3d()
             line["forms_configs"] = forms_configs()
             line["forms_stability"] = forms_stability()
+            line["forms_split"] = forms_split()
             line["forms_batched"] = forms_batched()
             line["forms_learned"] = forms_learned()
         print(json.dumps(line), flush=True)
