@@ -27,6 +27,10 @@
  *    the handle's stream, 0 means host memory (pageable or pinned).
  *  - Asynchrony: every call is enqueued on the handle's stream.  Calls that read or write host
  *    memory synchronise that stream before returning; device-pointer calls do not.
+ *  - Host buffers of init_fields and moments that are page-locked and mapped into the device's
+ *    address space (cudaHostAlloc, or cudaHostRegister with mapping) are read or written in place
+ *    by the kernels -- over NVLink-C2C on a GB300 -- instead of through a staging copy; pageable
+ *    host memory goes through device staging.  Either way the call returns after its work.
  *  - Errors: every call returns a lee_status; no call throws or aborts.  After LEE_ERR_CUDA or
  *    LEE_ERR_TIMEOUT the handle is poisoned: every later call except destroy returns
  *    LEE_ERR_POISONED.  lee_lbm_last_error() gives a one-line reason.

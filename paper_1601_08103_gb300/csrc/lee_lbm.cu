@@ -181,6 +181,21 @@ void free_all(lee_lbm *h) {
     cudaFree(h->mlp);
 }
 
+// Device address of a host buffer that kernels can use in place: page-locked host memory mapped
+// into the device address space (cudaHostAlloc, or cudaHostRegister with mapping), which a GB300
+// reaches over NVLink-C2C.  nullptr for pageable memory, whose bytes go through a staging copy.
+template <class T>
+T *mapped_host(T *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<T *>(a.devicePointer);
+}
+
 lee_status ensure_fields(lee_lbm *h) {
     if (h->fields) return LEE_OK;
     LEE_CK(h, cudaMalloc(&h->fields, sizeof(double) * (size_t)(h->D + 2) * (size_t)h->cells), "cudaMalloc(fields)");
@@ -335,7 +350,14 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
     if (s != LEE_OK) return s;
     if (!rho || !theta || (h->D > 0 && !u)) return fail(h, LEE_ERR_INVALID_ARGUMENT, "init_fields: NULL field");
     const double *dr = rho, *du = u, *dt = theta;
-    if (!on_device) {
+    const double *mr = on_device ? nullptr : mapped_host(rho), *mu = on_device ? nullptr : mapped_host(u),
+                 *mt = on_device ? nullptr : mapped_host(theta);
+    const bool in_place = mr && mt && (h->D == 0 || mu);
+    if (in_place) {  // the kernels read the mapped host fields directly
+        dr = mr;
+        du = mu;
+        dt = mt;
+    } else if (!on_device) {
         if ((s = ensure_fields(h)) != LEE_OK) return s;
         const size_t n = sizeof(double) * (size_t)h->cells;
         double *fr = h->fields, *fu = h->fields + h->cells, *ft = h->fields + (size_t)(h->D + 1) * h->cells;
@@ -481,6 +503,15 @@ lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, in
     if (on_device) {
         LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, rho, u, theta, h->st), "moments");
         return LEE_OK;
+    }
+    {
+        double *mr = mapped_host(rho), *mu = mapped_host(u), *mt = mapped_host(theta);
+        if ((!rho || mr) && (!u || mu) && (!theta || mt)) {  // write the mapped host buffers directly
+            LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, mr, mu, mt, h->st),
+                   "moments");
+            LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+            return LEE_OK;
+        }
     }
     if ((s = ensure_fields(h)) != LEE_OK) return s;
     double *fr = h->fields, *fu = h->fields + h->cells, *ft = h->fields + (size_t)(h->D + 1) * h->cells;
