@@ -117,6 +117,57 @@ __global__ void k_init_maxabs(const double *__restrict__ rho, const double *__re
     if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(m));
 }
 
+// Border cells of an open 2D grid, after a step that ran with zero-incoming edges: each is pulled
+// again, now with the entering populations of the learned edge (ghost[4][L]: x = 0, x = nx - 1,
+// y = 0, y = ny - 1, indexed along the edge), collided and stored over the zero-incoming result.
+// The pulls follow the fused step's open-edge rules and the collision is collide_cell, so the
+// state equals that of one step run with the ghosts throughout.  One thread per border cell
+// (corners belong to the x-edges).
+template <class S, class T>
+__global__ void k_edge_fixup(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
+                             CollideCoef<typename Store<T>::C> cf, OpenEdge<typename Store<T>::C> ob) {
+    static_assert(S::D == 2, "border fix-up of 2D grids");
+    using C = typename Store<T>::C;
+    const int nx = gd.nx, ny = gd.ny, L = ob.ghost_L;
+    const int nb = 2 * ny + 2 * (nx - 2);
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
+        int x, y;
+        if (r < ny) {
+            x = 0;
+            y = r;
+        } else if (r < 2 * ny) {
+            x = nx - 1;
+            y = r - ny;
+        } else if (r < 2 * ny + (nx - 2)) {
+            x = 1 + (r - 2 * ny);
+            y = 0;
+        } else {
+            x = 1 + (r - 2 * ny - (nx - 2));
+            y = ny - 1;
+        }
+        C pull[S::Q][1], post[S::Q][1];
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+            const int xs = x - cx, ys = y - cy;
+            C v = C(0);
+            if (ys < 0 || ys >= ny) {  // enters through the bottom (c_y = +1) or top edge
+                if (cx == 0 && ob.ghost) v = ob.ghost[(cy == 1 ? 2 : 3) * L + x];
+            } else if (xs < 0) {  // through the left edge
+                if (cy == 0 && ob.ghost) v = ob.ghost[0 * L + y];
+            } else if (xs >= nx) {  // through the right edge
+                if (cy == 0 && ob.ghost) v = ob.ghost[1 * L + y];
+            } else {
+                v = Store<T>::load(src[(long long)i * gd.pitch + (long long)ys * nx + xs]);
+            }
+            pull[i][0] = v;
+        });
+        collide_cell<S, 0>(pull, post, cf);
+#pragma unroll
+        for (int i = 0; i < S::Q; ++i) dst[(long long)i * gd.pitch + (long long)y * nx + x] = Store<T>::make(post[i][0]);
+    }
+}
+
 // Sponge damping of a stored post-collision state: g* <- (1 - sigma(d)) g* in the frame cells.
 // Applied once after init_fields so that the initial state is a post-collision state like every
 // later one (the equilibrium is its own collision; the frame damping is not).

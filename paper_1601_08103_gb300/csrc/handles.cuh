@@ -43,6 +43,9 @@ struct lee_lbm {
     // the stream they are captured on
     std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
     cudaStream_t cap = nullptr;
+    // learned edge: the network runs on `side` while the step runs on the handle's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // set by LEE_SINGLE_STEP=1 in the environment at create time: never fuse two steps per
     // launch (for comparisons against the one-step kernel)
     bool single_step_only = false;

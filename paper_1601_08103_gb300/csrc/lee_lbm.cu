@@ -418,17 +418,33 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.ghost_L = learned ? h->ghost_L : 0;
     L.force_scalar = h->force_scalar ? 1 : 0;
     L.store_scale = h->scale;
-    // One time step's launches (boundary network first for the learned edge) on stream `st`.
+    // One time step's launches on stream `st`.  Learned edge: the boundary network runs on a side
+    // stream while the step runs with zero-incoming edges on `st`; after the join the border
+    // cells are pulled again with the network's entering populations.  Interior cells never read
+    // the ghosts, so the state is that of a step run with the ghosts throughout.
+    if (learned && !h->side) {
+        LEE_CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
+        LEE_CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "fork event");
+        LEE_CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "join event");
+    }
     auto launch_step = [&](int from, cudaStream_t st) -> cudaError_t {
         L.src = h->buf[from];
         L.dst = h->buf[from ^ 1];
         L.stream = st;
-        if (learned) {
-            cudaError_t e = launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[from], h->pitch, (int)h->cfg.nx,
-                                                (int)h->cfg.ny, h->ghost, h->ghost_L, st);
-            if (e != cudaSuccess) return e;
-        }
-        return h->ops->step(L);
+        if (!learned) return h->ops->step(L);
+        cudaError_t e = cudaEventRecord(h->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[from], h->pitch, (int)h->cfg.nx, (int)h->cfg.ny,
+                                    h->ghost, h->ghost_L, h->side);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+        if (e != cudaSuccess) return e;
+        L.ghost = nullptr;  // the whole grid with zero-incoming edges
+        e = h->ops->step(L);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
+        L.ghost = h->ghost;
+        if (e == cudaSuccess) e = h->ops->edge_fixup(L);
+        return e;
     };
     int64_t left = n;
     // 1D grids that fit in shared memory: every step in one launch of the on-chip kernel
@@ -644,6 +660,12 @@ lee_status lee_lbm_destroy(lee_lbm *h) {
     cudaStreamSynchronize(h->st);
     for (auto &kv : h->exec) cudaGraphExecDestroy(kv.second);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     free_all(h);
     delete h;
     cudaGetLastError();

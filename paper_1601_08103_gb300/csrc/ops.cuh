@@ -57,6 +57,9 @@ struct SetOps {
     // all steps of a small 1D grid in one launch, in place on g (nullptr for 2D/3D sets);
     // returns cudaErrorInvalidValue when the grid does not fit in shared memory
     cudaError_t (*onchip_1d)(const StepLaunch &L, void *g, long long nsteps);
+    // border cells of an open 2D grid pulled again with the entering populations L.ghost and
+    // collided (after a step with zero-incoming edges); nullptr for 1D/3D sets
+    cudaError_t (*edge_fixup)(const StepLaunch &L);
     // sponge-frame damping of a stored state (after init_fields)
     cudaError_t (*sponge_damp)(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
                                cudaStream_t st);

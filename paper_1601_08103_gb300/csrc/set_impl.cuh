@@ -175,6 +175,23 @@ struct SetImpl {
     }
     static cudaError_t step2_prepare() { return two_step_prepare<S>(); }
     static cudaError_t step2(const StepLaunch &L) { return two_step_launch<S>(L); }
+    static cudaError_t edge_fixup(const StepLaunch &L) {
+        if constexpr (S::D != 2) {
+            return cudaErrorInvalidValue;
+        } else {
+            return with_storage(L.storage, [&](auto *tp) {
+                using T = std::remove_pointer_t<decltype(tp)>;
+                using C = typename Store<T>::C;
+                GridDesc gd{L.nx, L.ny, 1, L.nx, (long long)L.nx * L.ny, L.pitch};
+                const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
+                OpenEdge<C> ob{0, C(0), static_cast<const C *>(L.ghost), L.ghost_L};
+                const int nb = 2 * L.ny + 2 * (L.nx - 2);
+                k_edge_fixup<S, T><<<(nb + 127) / 128, 128, 0, L.stream>>>(static_cast<const T *>(L.src),
+                                                                          static_cast<T *>(L.dst), gd, cf, ob);
+                return cudaGetLastError();
+            });
+        }
+    }
     static SetOps make() {
         SetOps o{};
         o.D = S::D;
@@ -187,6 +204,7 @@ struct SetImpl {
         o.export_f64 = &export_f64;
         o.import_f64 = &import_f64;
         o.sponge_damp = &sponge_damp;
+        o.edge_fixup = S::D == 2 ? &edge_fixup : nullptr;
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         o.step2 = S::D == 2 ? &step2 : nullptr;
         o.step2_prepare = S::D == 2 ? &step2_prepare : nullptr;
