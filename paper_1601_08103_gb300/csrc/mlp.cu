@@ -400,7 +400,16 @@ __global__ void k_edge_inputs(const T *__restrict__ g, long long pitch, int NX, 
 
 // The learned boundary of one step: strips of the current post-collision state -> network ->
 // entering populations ghost[4][L] (arithmetic type C of the storage).
-constexpr int kBoundaryWarps = 2;  // small blocks: the 2 (nx + ny) border rows spread over many SMs
+//
+// One block of 4 warps per group of 16 border rows.  The chain of three dependent layers is what
+// bounds this kernel, so the hidden units are split over the warps: warp w computes hidden units
+// 16 w .. 16 w + 15 of layers 1 and 2 (two 8-column tiles each).  The C fragments of a warp's two
+// tiles are exactly the A fragment of k-chunk w of the next layer, and that per-lane layout is the
+// same in every warp, so the fragments pass between warps through shared memory as they are.
+// Warp 0 runs layer 3 over the four k-chunks in order and applies the passivity bound.  Every
+// tile sees the same operations in the same order as in mlp_forward_warp, so the result is the
+// same bit for bit.
+constexpr int kBoundaryWarps = 4;
 
 template <class T>
 __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG, const T *__restrict__ g, long long pitch,
@@ -408,13 +417,14 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG,
                                                                       typename Store<T>::C *__restrict__ ghost, int L) {
     using C = typename Store<T>::C;
     __shared__ __align__(16) unsigned char wsm[kStagedWeightBytes];
-    __shared__ float tile[kBoundaryWarps][16][kMlpIn];
-    __shared__ float sc[kBoundaryWarps][16];
+    __shared__ float tile[16][kMlpIn];
+    __shared__ float sc[16];
+    __shared__ uint32_t afrag1[kBoundaryWarps][32][4], afrag2[kBoundaryWarps][32][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = 2 * (NX + NY);
-    const int row0 = (blockIdx.x * kBoundaryWarps + warp) * 16;
-    if (lane < 16) {
-        const int r = row0 + lane;
+    const int row0 = blockIdx.x * 16;
+    if (threadIdx.x < 16) {
+        const int r = row0 + threadIdx.x;
         float xv[kMlpIn], s = 1.f;
         if (r < R) {
             strip_inputs<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, xv, s);
@@ -423,16 +433,74 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG,
             for (int k = 0; k < kMlpIn; ++k) xv[k] = 0.f;
         }
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) tile[warp][lane][k] = xv[k];
-        sc[warp][lane] = s;
+        for (int k = 0; k < kMlpIn; ++k) tile[threadIdx.x][k] = xv[k];
+        sc[threadIdx.x] = s;
     }
     const MlpDev W = stage_forward_weights(WG, wsm);  // ends with a block barrier
-    uint32_t ax[4];
-    a_frag_from_tile(tile[warp], ax);
-    MlpFwd F;
-    mlp_forward_warp(W, ax, F);
     const int gq = lane >> 2, t = lane & 3;
-    // Passivity bound over the warp's 16 border cells: the entering populations may carry at most
+    // layer 1, tiles 2w and 2w+1
+    {
+        uint32_t ax[4];
+        a_frag_from_tile(tile, ax);
+        uint32_t h[2][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = 2 * warp + q;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            const __nv_bfloat16 *w = W.w1 + (8 * j + gq) * kMlpIn + 2 * t;
+            mma16816(z, ax, ldw(w), ldw(w + 8));
+            const float bb0 = W.b1[8 * j + 2 * t], bb1 = W.b1[8 * j + 2 * t + 1];
+            z[0] += bb0;
+            z[1] += bb1;
+            z[2] += bb0;
+            z[3] += bb1;
+            h[q][0] = pack_bf16(gelu(z[0]), gelu(z[1]));
+            h[q][1] = pack_bf16(gelu(z[2]), gelu(z[3]));
+        }
+        afrag1[warp][lane][0] = h[0][0];
+        afrag1[warp][lane][1] = h[0][1];
+        afrag1[warp][lane][2] = h[1][0];
+        afrag1[warp][lane][3] = h[1][1];
+    }
+    __syncthreads();
+    // layer 2, tiles 2w and 2w+1, over the four k-chunks
+    {
+        uint32_t h[2][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = 2 * warp + q;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t a[4] = {afrag1[kk][lane][0], afrag1[kk][lane][1], afrag1[kk][lane][2], afrag1[kk][lane][3]};
+                const __nv_bfloat16 *w = W.w2 + (8 * j + gq) * kMlpHid + 16 * kk + 2 * t;
+                mma16816(z, a, ldw(w), ldw(w + 8));
+            }
+            const float bb0 = W.b2[8 * j + 2 * t], bb1 = W.b2[8 * j + 2 * t + 1];
+            z[0] += bb0;
+            z[1] += bb1;
+            z[2] += bb0;
+            z[3] += bb1;
+            h[q][0] = pack_bf16(gelu(z[0]), gelu(z[1]));
+            h[q][1] = pack_bf16(gelu(z[2]), gelu(z[3]));
+        }
+        afrag2[warp][lane][0] = h[0][0];
+        afrag2[warp][lane][1] = h[0][1];
+        afrag2[warp][lane][2] = h[1][0];
+        afrag2[warp][lane][3] = h[1][1];
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    float z3[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t a[4] = {afrag2[kk][lane][0], afrag2[kk][lane][1], afrag2[kk][lane][2], afrag2[kk][lane][3]};
+        const __nv_bfloat16 *w = W.w3 + gq * kMlpHid + 16 * kk + 2 * t;
+        mma16816(z3, a, ldw(w), ldw(w + 8));
+    }
+    const float b3 = W.b3[0];
+    const float y_lo = z3[0] + b3, y_hi = z3[2] + b3;  // column 0 lives in lanes with t == 0
+    // Passivity bound over the block's 16 border cells: the entering populations may carry at most
     // the weighted energy sum g^2 / f* of the outward populations leaving through the same cells
     // (canonical slot 2 at depth 0 of each strip; entering and leaving velocities share f*).  If
     // the network's predictions exceed it they are scaled down together.  The edge then never adds
@@ -442,8 +510,8 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG,
     for (int h = 0; h < 2; ++h) {
         const int lr = gq + 8 * h;
         const bool ok = (t == 0) && (row0 + lr < R);
-        const float hout = tile[warp][lr][2] * sc[warp][lr];
-        vin[h] = ok ? sc[warp][lr] * (h ? F.y_hi : F.y_lo) : 0.f;
+        const float hout = tile[lr][2] * sc[lr];
+        vin[h] = ok ? sc[lr] * (h ? y_hi : y_lo) : 0.f;
         ein += vin[h] * vin[h];
         eout += ok ? hout * hout : 0.f;
     }
@@ -485,7 +553,7 @@ cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, 
                                 int L, cudaStream_t st) {
     const MlpDev W = mlp_dev(packed);
     const int R = 2 * (NX + NY);
-    const int blocks = (R + 16 * kBoundaryWarps - 1) / (16 * kBoundaryWarps);
+    const int blocks = (R + 15) / 16;  // one block per 16 border rows
     return with_store(storage, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         using C = typename Store<T>::C;
