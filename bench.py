@@ -307,9 +307,16 @@ def cpu_baseline(budget_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.step(SET, (NX, NX, 1), TAU, g, n)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, a few steps of the same grid (reported beside, not the value)
     oracle.set_threads(1)
+    n1 = 4
+    t0 = time.perf_counter()
+    oracle.step(SET, (NX, NX, 1), TAU, g, n1)
+    dt1 = time.perf_counter() - t0
     return {"value": round(NX * NX * n / dt / 1e6, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{NX}x{NX} D2Q5 FP64, {n} steps, {cores} OpenMP threads, {dt:.1f} s"}
+            "sample": f"{NX}x{NX} D2Q5 FP64, {n} steps, {cores} OpenMP threads, {dt:.1f} s",
+            "single_thread": {"value": round(NX * NX * n1 / dt1 / 1e6, 2), "unit": "MLUPS",
+                              "sample": f"{NX}x{NX} D2Q5 FP64, {n1} steps, 1 thread, {dt1:.1f} s"}}
 
 
 def forms_3d():
