@@ -469,7 +469,9 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
     });
 
     C post[S::Q][V];
-    collide_chunk<S>(pull, post, cf);
+    // one cell at a time: this kernel streams at the memory bound, and the packed f32x2 pairs
+    // (same bits) cost it 9 to 12 registers and occupancy
+    collide_chunk<S, false>(pull, post, cf);
 
     if constexpr (OPEN) {
         if (ob.sponge_w > 0) {
