@@ -565,7 +565,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ sr
 // bit for bit.  DRAM sees one read and one write of every population per two steps, plus two
 // halo rows above and below each tile that the neighbouring tiles (running at the same time)
 // mostly serve from L2.  The ring is the only shared memory: 3 x 4 x q x (128 + 8) floats,
-// 32.6 KB for D2Q5, so six blocks (24 warps) fit on an SM.
+// 32.6 KB for D2Q5; with the registers of the load prefetch (below) five blocks (20 warps) fit on
+// an SM.
 constexpr int kTbW = 128;
 constexpr int kTbV = kTbW / 32;            // cells per lane
 constexpr int kTbRow = kTbW + 8;           // ring row: columns x0-4 .. x0+131 (x0-1 .. x0+128 used)
