@@ -1,6 +1,7 @@
 // set_impl.cuh -- host launchers for one velocity set, instantiated by the set_*.cu units.
 #pragma once
 
+#include "onchip_cluster.cuh"
 #include "split.cuh"
 #include "step_launch.cuh"
 
@@ -166,6 +167,33 @@ struct SetImpl {
                 if (e != cudaSuccess) return e;
                 const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
                 OpenEdge<C> ob{L.sponge_w, (C)L.sponge_smax, nullptr, 0};
+                if (L.nx >= 64 * kOnchipCluster) {
+                    // a cluster of kOnchipCluster CTAs, one segment each (onchip_cluster.cuh)
+                    const int seg = (L.nx + kOnchipCluster - 1) / kOnchipCluster;
+                    const size_t csmem = 2 * sizeof(T) * (size_t)S::Q * (size_t)seg;
+                    e = cudaFuncSetAttribute(k_onchip_1d_cluster<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)csmem);
+                    if (e == cudaSuccess && kOnchipCluster > 8)  // clusters above 8 CTAs are opt-in
+                        e = cudaFuncSetAttribute(k_onchip_1d_cluster<S, T>,
+                                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                    if (e != cudaSuccess) return e;
+                    cudaLaunchConfig_t lc = {};
+                    lc.gridDim = dim3(kOnchipCluster);
+                    lc.blockDim = dim3(seg < 1024 ? ((seg + 31) / 32) * 32 : 1024);
+                    lc.dynamicSmemBytes = csmem;
+                    lc.stream = L.stream;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeClusterDimension;
+                    attr[0].val.clusterDim.x = kOnchipCluster;
+                    attr[0].val.clusterDim.y = 1;
+                    attr[0].val.clusterDim.z = 1;
+                    lc.attrs = attr;
+                    lc.numAttrs = 1;
+                    e = cudaLaunchKernelEx(&lc, k_onchip_1d_cluster<S, T>, static_cast<T *>(g), L.nx, L.pitch, cf, ob,
+                                           L.open, nsteps);
+                    if (e != cudaSuccess) return e;
+                    return cudaGetLastError();
+                }
                 const int threads = L.nx < 1024 ? ((L.nx + 31) / 32) * 32 : 1024;
                 k_onchip_1d<S, T><<<1, threads, smem, L.stream>>>(static_cast<T *>(g), L.nx, L.pitch, cf, ob, L.open,
                                                                   nsteps);
