@@ -153,20 +153,23 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out);
 
 /* Sets the state to the equilibrium of the given fields, g_i = g_i^eq(rho', u', theta')
  * (Sec. 7 initial condition; Sec. 4/5 equilibrium).  rho[cells], u[D][cells], theta[cells] in
- * FP64.  For 16-bit storage with store_scale = 0 the scale S is chosen here: the largest power of
- * two with S * max_i,x |g_i / f*_i| <= 1024. */
+ * FP64.  For 16-bit and split storage with store_scale = 0 the scale S is chosen here: the
+ * largest power of two with S * max_i,x |g_i^eq / f*_i| <= 1024. */
 lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, const double *theta, int32_t on_device);
 
 /* Advances n >= 0 time steps of the LBE update scheme (Sec. 6): one fused pull-stream + BGK
- * collision kernel per step (plus the boundary network for OPEN_LEARNED).  Asynchronous.  For
- * n >= 8 the launches are replayed from a CUDA graph (one graph holding all n steps for
- * n <= 4096, else repeated 100-step graphs), captured on first use of that length on a private
- * stream and cached in the handle; results are identical to direct launches.  Periodic 2D FP32
- * grids with nx a multiple of 4 advance two steps per launch (lee_lbm_steps_per_launch).  A 1D
- * grid whose
- * two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB, e.g. D1Q3 FP64 up
- * to 4843 cells) runs all n >= 2 steps in one launch of a single-block kernel instead, again
- * with identical results. */
+ * collision kernel per step.  Asynchronous.  For n >= 8 the launches are replayed from a CUDA
+ * graph (one graph holding all n steps for n <= 4096, else repeated 100-step graphs), captured on
+ * first use of that length on a private stream and cached in the handle; results are identical to
+ * direct launches.  Every form below also gives the same bits as single one-step launches:
+ *  - periodic 2D FP32 grids with nx a multiple of 4 advance two steps per launch
+ *    (lee_lbm_steps_per_launch);
+ *  - a 1D grid whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
+ *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
+ *    512 cells a thread-block cluster of 8 blocks;
+ *  - OPEN_LEARNED: the boundary network runs on a second stream while the step runs with
+ *    zero-incoming edges; the border cells are then pulled again with the network's entering
+ *    populations and collided (the stream waits for both before returning work to the caller). */
 lee_status lee_lbm_step(lee_lbm *h, int64_t n);
 
 /* Per-cell moments of the current state (Sec. 4 discrete moments; Sec. 5 temperature for
