@@ -37,7 +37,10 @@ STORAGE = "f32"
 BYTES_PER_LUP = 2 * 5 * 4  # read + write of q = 5 FP32 populations (algorithmic)
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = "2D D2Q5 periodic 2048x2048, FP32, tau=0.6, pulse+8 plane waves, 1000 steps/job"
-PROFILE = os.path.join(ROOT, "profiles", "stream_collide_2step_d2q5_f32_2048x2048.md")
+# ncu summary of the stream-collide kernel the benchmark runs, by time steps fused per launch
+PROFILES = {k: os.path.join(ROOT, "profiles", f"stream_collide_{k}step_d2q5_f32_2048x2048.md") for k in (1, 2, 3, 4)}
+KERNEL_NAMES = {1: "k_stream_collide<D2Q5,float,V=4,periodic>", 2: "k_stream_collide_2step<D2Q5,float>",
+                3: "k_stream_collide_kstep<D2Q5,K=3,float>", 4: "k_stream_collide_kstep<D2Q5,K=4,float>"}
 KERNEL_SOURCES = ["paper_1601_08103_gb300/csrc/kernels.cuh", "paper_1601_08103_gb300/csrc/step_launch.cuh",
                   "paper_1601_08103_gb300/csrc/velsets.cuh"]
 
@@ -50,12 +53,14 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per stream-collide launch from the committed ncu summary, or None if the
-    summary is missing or was taken on different kernel sources."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(steps_per_launch: int):
+    """DRAM bytes per stream-collide launch from the committed ncu summary of the kernel that
+    fuses this many steps, or None if the summary is missing or was taken on different kernel
+    sources."""
+    path = PROFILES.get(steps_per_launch)
+    if not path or not os.path.exists(path):
         return None
-    txt = open(PROFILE).read()
+    txt = open(path).read()
     sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not sha or not tr or sha.group(1) != kernel_source_sha():
@@ -186,10 +191,12 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sv = lee.Solver(SET, (NX, NX, 1), TAU, storage=STORAGE, stream=stream)
 
-    # steps per stream-collide launch: 2 for this periodic 2D FP32 grid (two fused time steps per
-    # launch, the intermediate state in shared memory), 1 for the one-step kernel
+    # steps per stream-collide launch: 3 for this periodic 2D FP32 grid (three fused time steps
+    # per launch, the intermediate states in shared memory), 1 for the one-step kernel.  A job of
+    # NSTEPS steps is NSTEPS // spl fused launches and NSTEPS % spl single steps; every launch reads
+    # and writes the whole state once, so each moves the same algorithmic bytes.
     spl = max(sv.steps_per_launch, 1)
-    step_launches = NSTEPS // spl
+    step_launches = NSTEPS // spl + NSTEPS % spl
     launches_per_step = 1 + step_launches + 1 + 2  # init, steps, moments, reduce (partial + final)
 
     def one_step(ev):
@@ -257,7 +264,7 @@ def run_ours(args, rank, world, local):
 
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_LUP * cells / kernel_avg_s / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(spl)
     line = {
         "metric": "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline",
         "value": round(value, 1),
@@ -277,9 +284,9 @@ def run_ours(args, rank, world, local):
                    "wall_s_timed_region": round(wall, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": ("k_stream_collide_2step<D2Q5,float>" if spl == 2
-                                else "k_stream_collide<D2Q5,float,V=4,periodic>"),
+                     "kernel": KERNEL_NAMES.get(spl, "?"),
                      "steps_per_launch": spl,
+                     "launches_per_job": {"fused": NSTEPS // spl, "single_step": NSTEPS % spl},
                      "algorithmic_bytes_per_launch": BYTES_PER_LUP * cells,
                      "avg_launch_us": round(kernel_avg_s * 1e6, 3)},
         "e2e": {"value": round(e2e_value, 1), "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -48,9 +48,10 @@ lee_status lee_batch_init_fields(lee_batch *b, int32_t d, const double *rho, con
  * LAUNCH call runs the autotuner unless lee_batch_set_tuning fixed the launch shape.  In GRAPH
  * mode a run of up to 4096 steps is one launch of a graph holding all its steps (captured on
  * first use of that length and parity, then cached); longer runs replay a 100-step graph.  With
- * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance two steps per
- * launch (the intermediate state kept in shared memory; tiles of 128 columns x up to 128 rows,
- * dispatched largest first), bit-identical to single steps. */
+ * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance four steps per
+ * launch (the intermediate states kept in shared memory; tiles of 128 columns x up to 128 rows,
+ * dispatched largest first; LEE_TB_STEPS=1..4 in the environment at create time picks another
+ * count), bit-identical to single steps. */
 lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode);
 
 /* Per-cell moments of domain d (as lee_lbm_moments).  NULL outputs are skipped. */

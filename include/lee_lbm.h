@@ -162,8 +162,10 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  * graph (one graph holding all n steps for n <= 4096, else repeated 100-step graphs), captured on
  * first use of that length on a private stream and cached in the handle; results are identical to
  * direct launches.  Every form below also gives the same bits as single one-step launches:
- *  - periodic 2D FP32 grids with nx a multiple of 4 advance two steps per launch
- *    (lee_lbm_steps_per_launch);
+ *  - periodic 2D FP32 grids with nx a multiple of 4 advance four steps per launch, the three
+ *    intermediate states kept in shared memory (temporal blocking; LEE_TB_STEPS=1..4 in the
+ *    environment at create time picks another count; lee_lbm_steps_per_launch reports it); a
+ *    run of n steps is n / 4 such launches and n % 4 single steps;
  *  - a 1D grid whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
@@ -207,9 +209,10 @@ lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t npa
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
 
 /* How lee_lbm_step runs this grid: *steps = 1 (one fused stream-collide launch per time step),
- * 2 (periodic 2D FP32 grids with nx a multiple of 4: two time steps per launch, the
- * intermediate state kept in shared memory -- temporal blocking) or 0 (small 1D grid: all steps
- * of a call in one on-chip launch).  All forms give bit-identical results. */
+ * 2..4 (periodic 2D FP32 grids with nx a multiple of 4: that many time steps per launch, the
+ * intermediate states kept in shared memory -- temporal blocking; 4 unless LEE_TB_STEPS was set
+ * at create time) or 0 (small 1D grid: all steps of a call in one on-chip launch).  All forms
+ * give bit-identical results. */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);
 
 /* The 16-bit storage scale S in use (1 for F64/F32 storage). */

@@ -49,18 +49,33 @@ cudaError_t launch_batched_2step(const void *src, void *dst, const void *doms, c
     return cudaGetLastError();
 }
 
-// Resident blocks of the batched two-step kernel on the current device (sets its shared-memory
-// attribute; called outside any stream capture).
+template <class S, int K>
+cudaError_t launch_batched_kstep(const void *src, void *dst, const void *doms, const void *tiles, int nblocks,
+                                 cudaStream_t st) {
+    k_stream_collide_kstep_batched<S, K><<<nblocks, 128, tbk_smem_bytes<S, K>(), st>>>(
+        static_cast<const float *>(src), static_cast<float *>(dst), static_cast<const TbDomain *>(doms),
+        static_cast<const int3 *>(tiles));
+    return cudaGetLastError();
+}
+
+// Sets the shared-memory attribute of the batched multi-step kernel fusing `unit` steps on the
+// current device (outside any stream capture) and returns its launcher.
 template <class S>
-cudaError_t prepare_batched_2step(int *capacity) {
-    constexpr int smem = tb_smem_bytes<S>();
-    cudaError_t e = cudaFuncSetAttribute(k_stream_collide_2step_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0, dev = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_2step_batched<S>, 128, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    *capacity = per_sm * sms > 0 ? per_sm * sms : 1;
+cudaError_t prepare_batched_tb(int unit, lee::BatchedTbFn *fn) {
+    cudaError_t e = cudaErrorInvalidValue;
+    if (unit == 2) {
+        e = cudaFuncSetAttribute(k_stream_collide_2step_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tb_smem_bytes<S>());
+        *fn = &launch_batched_2step<S>;
+    } else if (unit == 3) {
+        e = cudaFuncSetAttribute(k_stream_collide_kstep_batched<S, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tbk_smem_bytes<S, 3>());
+        *fn = &launch_batched_kstep<S, 3>;
+    } else if (unit == 4) {
+        e = cudaFuncSetAttribute(k_stream_collide_kstep_batched<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tbk_smem_bytes<S, 4>());
+        *fn = &launch_batched_kstep<S, 4>;
+    }
     return e;
 }
 
@@ -277,15 +292,14 @@ lee_status tune(lee_batch *b) {
     return LEE_OK;
 }
 
-// Two-step tiles of 128 columns x at most kBatchTileRows rows (fewer for short domains), listed
-// largest first so that the block scheduler balances the uneven domains.
+// Multi-step tiles of 128 columns x at most kBatchTileRows rows (fewer for short domains),
+// listed largest first so that the block scheduler balances the uneven domains.
 constexpr int kBatchTileRows = 128;
 
-lee_status build_tb(lee_batch *b) {
-    int capacity = 1;
-    cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_2step<D2Q5>(&capacity) : prepare_batched_2step<D2Q5Di>(&capacity);
-    if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, std::string("two-step prepare: ") + cudaGetErrorString(e));
-    b->tb_fn = b->set == LEE_D2Q5 ? &launch_batched_2step<D2Q5> : &launch_batched_2step<D2Q5Di>;
+lee_status build_tb(lee_batch *b, int unit) {
+    cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_tb<D2Q5>(unit, &b->tb_fn)
+                                       : prepare_batched_tb<D2Q5Di>(unit, &b->tb_fn);
+    if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, std::string("multi-step prepare: ") + cudaGetErrorString(e));
     std::vector<TbDomain> hd(b->count);
     struct Tile {
         int rows, d, x0, y0;
@@ -311,21 +325,20 @@ lee_status build_tb(lee_batch *b) {
     std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &p, const Tile &q) { return p.rows > q.rows; });
     std::vector<int3> ht(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) ht[k] = make_int3(tiles[k].d, tiles[k].x0, tiles[k].y0);
-    BCK(b, cudaMalloc(&b->d_tb, sizeof(TbDomain) * hd.size()), "cudaMalloc(two-step domains)");
-    BCK(b, cudaMalloc(&b->d_tb_tiles, sizeof(int3) * ht.size()), "cudaMalloc(two-step tiles)");
+    BCK(b, cudaMalloc(&b->d_tb, sizeof(TbDomain) * hd.size()), "cudaMalloc(multi-step domains)");
+    BCK(b, cudaMalloc(&b->d_tb_tiles, sizeof(int3) * ht.size()), "cudaMalloc(multi-step tiles)");
     BCK(b, cudaMemcpyAsync(b->d_tb, hd.data(), sizeof(TbDomain) * hd.size(), cudaMemcpyHostToDevice, b->st), "H2D");
     BCK(b, cudaMemcpyAsync(b->d_tb_tiles, ht.data(), sizeof(int3) * ht.size(), cudaMemcpyHostToDevice, b->st), "H2D");
     BCK(b, cudaStreamSynchronize(b->st), "sync");
-    (void)capacity;
     b->tb_blocks = (int)ht.size();
-    b->two = true;
+    b->unit = unit;
     return LEE_OK;
 }
 
-// One launch of the step unit (two fused steps when b->two, else one step) reading buffer
-// src_which and writing the other one.
+// One launch of the step unit (b->unit fused steps, or one step) reading buffer src_which and
+// writing the other one.
 cudaError_t launch_unit(lee_batch *b, int src_which, cudaStream_t st) {
-    if (b->two) return b->tb_fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_tb, b->d_tb_tiles, b->tb_blocks, st);
+    if (b->unit > 1) return b->tb_fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_tb, b->d_tb_tiles, b->tb_blocks, st);
     return b->fn(b->buf[src_which], b->buf[src_which ^ 1], b->d_doms, b->d_table, b->nblocks, b->threads, st);
 }
 
@@ -338,7 +351,7 @@ lee_status ensure_graph(lee_batch *b, int parity, long long steps, cudaGraphExec
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     int w = parity;
-    const int unit = b->two ? 2 : 1;
+    const int unit = b->unit;
     for (long long k = 0; k < steps / unit; ++k) {
         cudaError_t e = launch_unit(b, w, b->cap);
         if (e != cudaSuccess) {
@@ -425,10 +438,18 @@ lee_status lee_batch_create(int32_t set, int32_t storage, const lee_batch_domain
         cudaGetLastError();
         return s;
     }
-    bool two = storage == LEE_STORE_F32 && !(std::getenv("LEE_SINGLE_STEP") && std::getenv("LEE_SINGLE_STEP")[0] == '1');
-    for (int d = 0; d < count; ++d) two = two && domains[d].nx % 4 == 0 && domains[d].ny >= 3;
-    if (two) {
-        lee_status s2 = build_tb(b);
+    // time steps fused per launch: 4, or LEE_TB_STEPS=1..4 / LEE_SINGLE_STEP=1 at create time
+    int unit = 4;
+    if (const char *ev = std::getenv("LEE_TB_STEPS")) {
+        if (ev[0] >= '1' && ev[0] <= '4' && ev[1] == 0) unit = ev[0] - '0';
+    }
+    if (const char *ev = std::getenv("LEE_SINGLE_STEP")) {
+        if (ev[0] == '1') unit = 1;
+    }
+    bool fuse = storage == LEE_STORE_F32 && unit > 1;
+    for (int d = 0; d < count; ++d) fuse = fuse && domains[d].nx % 4 == 0 && domains[d].ny >= 3;
+    if (fuse) {
+        lee_status s2 = build_tb(b, unit);
         if (s2 != LEE_OK) {
             lee_batch_destroy(b);
             cudaGetLastError();
@@ -489,7 +510,7 @@ lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode) {
         return LEE_OK;
     }
     if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
-    const int unit = b->two ? 2 : 1;
+    const int unit = b->unit;
     int64_t units = n / unit;
     if (mode == LEE_BATCH_GRAPH) {
         // up to kMaxGraphSteps steps: one graph of all of them (one launch of the whole run);

@@ -46,9 +46,10 @@ struct lee_lbm {
     // learned edge: the network runs on `side` while the step runs on the handle's stream
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // set by LEE_SINGLE_STEP=1 in the environment at create time: never fuse two steps per
-    // launch (for comparisons against the one-step kernel)
-    bool single_step_only = false;
+    // time steps fused per launch on periodic 2D FP32 grids (temporal blocking): 4 by default;
+    // LEE_TB_STEPS=1..4 in the environment at create time overrides it, and LEE_SINGLE_STEP=1
+    // sets 1 (for comparisons between the one-, two-, three- and four-step kernels)
+    int tb_steps = 4;
     // set by LEE_FORCE_SCALAR=1 at create time: one cell per thread in every step kernel, and one
     // step per launch (for comparisons of the vector and packed paths against the scalar one)
     bool force_scalar = false;
@@ -56,6 +57,7 @@ struct lee_lbm {
 
 namespace lee {
 using BatchedFn = cudaError_t (*)(const void *, void *, const void *, const unsigned short *, int, int, cudaStream_t);
+using BatchedTbFn = cudaError_t (*)(const void *, void *, const void *, const void *, int, cudaStream_t);
 }
 
 struct lee_batch {
@@ -76,12 +78,13 @@ struct lee_batch {
     unsigned short *d_table = nullptr;
     size_t d_doms_cap = 0, d_table_cap = 0;
     lee::BatchedFn fn = nullptr;
-    // two fused steps per launch (FP32, every nx % 4 == 0): per-domain tiles and block table
-    bool two = false;
+    // time steps per launch: 1, or 2..4 fused (FP32, every nx % 4 == 0) with per-domain tiles and
+    // a block table
+    int unit = 1;
     void *d_tb = nullptr;
     void *d_tb_tiles = nullptr;  // int3 (domain, x0, y0) per block, largest tiles first
     int tb_blocks = 0;
-    cudaError_t (*tb_fn)(const void *, void *, const void *, const void *, int, cudaStream_t) = nullptr;
+    lee::BatchedTbFn tb_fn = nullptr;
     // captured graphs, keyed by (starting parity, number of steps); every graph has an even
     // number of steps, so replaying it leaves the buffer parity unchanged
     static constexpr int kMaxGraphSteps = 4096;

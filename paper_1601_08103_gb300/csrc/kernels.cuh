@@ -777,6 +777,227 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
     tb_tile<S, false>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
 }
 
+// ---------------------------------------------------------------------------------------------
+// K time steps per launch (deeper temporal blocking), periodic 2D FP32 grids with nx % 4 == 0
+// ---------------------------------------------------------------------------------------------
+// The two-step tile generalised to K levels (K = 4 by default, 3 on request).  Level l
+// (1 <= l < K) is S(t+l) on rows y0-(K-l) .. y0+H-1+(K-l) and columns x0-(K-l) .. x0+127+(K-l)
+// of the tile; it lives in its own 2-slot ring of 4-row blocks (block j of level l holds rows
+// y0-(K-l)+4j .. y0-(K-l)+4j+3, one per warp).  Level K is the output tile, stored to global
+// memory.  Iteration k runs
+//   level 1, block k: pulled from S(t) in global memory (loads issued one iteration ahead);
+//   barrier;
+//   level l = 2 .. K-1, block k-(l-1): pulled from blocks k-(l-1) and k-l+2 of level l-1; barrier;
+//   level K, block k-(K-1): likewise, and stored.
+// Level l, block j reads blocks j+1 (written in the interval just before) and j (one iteration
+// earlier) of level l-1, and overwrites the slot of its own block j-2, which level l+1 last read
+// one iteration earlier; so two slots per ring suffice with one barrier per level: K-1 barriers
+// per iteration and H/4 + K - 1 iterations per tile.  The K-l halo columns on each side of level l belong to lanes
+// 0 .. 2(K-l)-1, one cell each.  Every level is rounded to FP32 exactly like a stored state, so
+// the result equals K single steps bit for bit.  Shared memory: K-1 rings of 2 x 4 x q x (128+8)
+// floats, 65.3 KB for four levels of D2Q5 (three blocks = 12 warps per SM).
+//
+// Measured on GB300 (D2Q5, GLUPS on 2048^2 / 4096^2 / 8192^2): two steps per launch 284 / 298 /
+// 290; three levels with 3-slot rings and one barrier per iteration 351 / 388 / 409; four levels
+// that way (98 KB, two blocks per SM) 352 / 392 / 365; four levels with 2-slot rings 391 / 475 /
+// 499; five levels with 2-slot rings (87 KB, two blocks per SM) 396 / 429 / 395.  The kernel is
+// bound by instruction issue and latency, not DRAM (ncu: issue slots half busy, 12 warps per
+// SM), so the level count that keeps three blocks resident wins.  Giving each level's halo cells
+// of all four rows to one warp (4x fewer halo collisions) lost 5-18 %: the barriers then wait
+// for that warp.
+template <class S, int K>
+constexpr int tbk_smem_bytes() {
+    return (K - 1) * 2 * 4 * S::Q * kTbRow * (int)sizeof(float);
+}
+template <int K>
+constexpr int tbk_min_blocks() {
+    return K == 3 ? 5 : 3;
+}
+
+template <class S, int K, bool PF>
+__device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
+                                         long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
+                                         float *smem) {
+    static_assert(S::D == 2 && K >= 3 && K <= 4, "deep tiles are 2D with three or four levels");
+    constexpr int Q = S::Q;
+    // row of level l (1 .. K-1), ring block blk, warp row w, velocity i; column x0 at offset 4
+    auto ring = [&](int l, int blk, int w, int i) {
+        return smem + ((((l - 1) * 2 + (blk & 1)) * 4 + w) * Q + i) * kTbRow;
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int iters = H / 4 + K - 1;
+    auto wrap_x = [&](int x) {
+        x %= nx;
+        return x < 0 ? x + nx : x;
+    };
+    const int xa = wrap_x(x0 + kTbV * lane);
+    // the element a lane's float4 lacks: column x0-1 for lane 0 (c_x = +1), x0+128 for lane 31
+    // (c_x = -1)
+    const int xedge = wrap_x(lane == 0 ? x0 - 1 : x0 + kTbW);
+    // Halo cells of a level with h halo columns per side: lane L < 2h owns the cell at offset
+    // hoff(h) from x0.  Every lane computes the cell of lane L mod 2h (the same columns, so the
+    // loads coalesce) and only lanes L < 2h store it: the halo work has no branch and its
+    // collision interleaves with the main one.
+    auto hoff = [&](int h) {
+        const int idx = lane % (2 * h);
+        return idx < h ? idx - h : kTbW + idx - h;
+    };
+    // level 1 (h = K-1): the halo cell pulls velocity i from column x0 + o - c_x = xh[1 - c_x]
+    int xh[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) xh[e] = wrap_x(x0 + hoff(K - 1) - 1 + e);
+
+    struct Pre {
+        float4 t[Q];     // the lane's four cells of velocity i from row a - c_y
+        float edge[Q];   // lanes 0 and 31: the element the float4 lacks
+        float halo[Q];   // the level-1 halo cell's pull of velocity i
+    };
+    Pre pre;
+    const int lim1 = y0 + H + K - 2;  // last level-1 row the tile needs
+    int rn = (y0 - (K - 1) + warp) % ny;
+    if (rn < 0) rn += ny;
+    auto load_a = [&](int k) {  // called once for each k = 0, 1, 2, ... in this order
+        const int a = y0 - (K - 1) + 4 * k + warp;
+        if (a <= lim1) {
+            const int rows[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};  // a-1, a, a+1
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+                const float *rowp = src + (long long)i * pitch + (long long)rows[1 - cy] * nx;
+                pre.t[i] = __ldg(reinterpret_cast<const float4 *>(rowp + xa));
+                if constexpr (cx == 1) {
+                    if (lane == 0) pre.edge[i] = __ldg(rowp + xedge);
+                } else if constexpr (cx == -1) {
+                    if (lane == 31) pre.edge[i] = __ldg(rowp + xedge);
+                }
+                pre.halo[i] = __ldg(rowp + xh[1 - cx]);
+            });
+        }
+        rn += 4;
+        while (rn >= ny) rn -= ny;
+        if constexpr (PF) {
+            if ((lane & 7) == 0 && a + 4 <= lim1) {
+                const int rows2[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cy = S::c(i, 1);
+                    prefetch_l2(src + (long long)i * pitch + (long long)rows2[1 - cy] * nx + xa);
+                });
+            }
+        }
+    };
+    load_a(0);
+
+    // level l >= 2 (or K), block j: the lane's cells pulled from blocks j, j+1 of level l-1
+    auto pull_level = [&](int l, int j, float (&pb)[Q][kTbV]) {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+            const int rr = 4 * j + warp + 1 - cy;  // row within the blocks of level l-1
+            tb_pull<cx>(ring(l - 1, rr >> 2, rr & 3, i), lane, pb[i]);
+        });
+    };
+    // level l >= 2, block j: the halo cell at offset o, pulled from level l-1
+    auto pull_halo = [&](int l, int j, int o, float (&hin)[Q][1]) {
+        static_for<Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+            const int rr = 4 * j + warp + 1 - cy;
+            hin[i][0] = ring(l - 1, rr >> 2, rr & 3, i)[4 + o - cx];
+        });
+    };
+
+    for (int k = 0; k < iters; ++k) {
+        // level 1, block k
+        if (y0 - (K - 1) + 4 * k + warp <= lim1) {  // warp-uniform
+            float pa[Q][kTbV];
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0);
+                const float4 t = pre.t[i];
+                if constexpr (cx == 0) {
+                    pa[i][0] = t.x; pa[i][1] = t.y; pa[i][2] = t.z; pa[i][3] = t.w;
+                } else if constexpr (cx == 1) {
+                    float left = __shfl_up_sync(kFull, t.w, 1);
+                    if (lane == 0) left = pre.edge[i];
+                    pa[i][0] = left; pa[i][1] = t.x; pa[i][2] = t.y; pa[i][3] = t.z;
+                } else {
+                    float right = __shfl_down_sync(kFull, t.x, 1);
+                    if (lane == 31) right = pre.edge[i];
+                    pa[i][0] = t.y; pa[i][1] = t.z; pa[i][2] = t.w; pa[i][3] = right;
+                }
+            });
+            float hin[Q][1];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) hin[i][0] = pre.halo[i];
+            float post[Q][kTbV], hout[Q][1];
+            collide_chunk<S, kTbPacked>(pa, post, cf);
+            collide_chunk<S, kTbPacked>(hin, hout, cf);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) tb_st(ring(1, k, warp, i) + kTbV * lane + 4, post[i]);
+            if (lane < 2 * (K - 1)) {
+                const int o = hoff(K - 1);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) ring(1, k, warp, i)[4 + o] = hout[i][0];
+            }
+        }
+        if (k + 1 < iters) load_a(k + 1);
+        __syncthreads();  // level-1 block k visible; every read of the slots written below is done
+        static_for<K - 2>([&](auto Lx) {
+            constexpr int l = 2 + decltype(Lx)::value;
+            const int j = k - (l - 1);
+            if (j >= 0 && y0 - (K - l) + 4 * j + warp <= y0 + H - 1 + (K - l)) {  // warp-uniform
+                const int o = hoff(K - l);
+                float pb[Q][kTbV], post[Q][kTbV], hin[Q][1], hout[Q][1];
+                pull_level(l, j, pb);
+                pull_halo(l, j, o, hin);
+                collide_chunk<S, kTbPacked>(pb, post, cf);
+                collide_chunk<S, kTbPacked>(hin, hout, cf);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) tb_st(ring(l, j, warp, i) + kTbV * lane + 4, post[i]);
+                if (lane < 2 * (K - l)) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) ring(l, j, warp, i)[4 + o] = hout[i][0];
+                }
+            }
+            __syncthreads();  // level l block j visible to level l+1
+        });
+        const int m = k - (K - 1);
+        if (m >= 0) {
+            float pb[Q][kTbV], post[Q][kTbV];
+            pull_level(K, m, pb);
+            collide_chunk<S, kTbPacked>(pb, post, cf);
+            const int d = y0 + 4 * m + warp;
+            if (d < ny && x0 + kTbV * lane < nx) {
+                float *outp = dst + (long long)d * nx + x0 + kTbV * lane;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
+            }
+        }
+    }
+}
+
+template <class S, int K, bool PF>
+__global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kstep(const float *__restrict__ src,
+                                                                                float *__restrict__ dst, int nx,
+                                                                                int ny, long long pitch, int H,
+                                                                                CollideCoef<float> cf) {
+    extern __shared__ __align__(16) float tb_smem[];
+    tbk_tile<S, K, PF>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
+}
+
+// K fused steps over many periodic domains: block b works on tile tiles[b] = (domain, x0, y0)
+// of height doms[domain].H, exactly as the two-step batched kernel.
+template <class S, int K>
+__global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kstep_batched(
+    const float *__restrict__ src, float *__restrict__ dst, const TbDomain *__restrict__ doms,
+    const int3 *__restrict__ tiles) {
+    extern __shared__ __align__(16) float tb_smem[];
+    const int3 tl = tiles[blockIdx.x];
+    const TbDomain &D = doms[tl.x];
+    tbk_tile<S, K, false>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
+}
+
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
 // blocks [first_block[d], first_block[d+1]); its populations start at element offset[d] of the
 // shared buffers, and it has its own extents and relaxation coefficients (its own tau).  The

@@ -127,6 +127,15 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
     return s;
 }
 
+// Time steps fused per launch: tb_steps on periodic 2D FP32 grids whose width is a multiple of 4
+// (temporal blocking), one step otherwise.
+int fused_steps(const lee_lbm *h) {
+    const bool tiled = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
+                       h->cfg.nx % 4 == 0 && h->cfg.ny >= 3;
+    if (!tiled || h->tb_steps <= 1) return 1;
+    return h->tb_steps >= 3 && h->ops->stepk ? h->tb_steps : 2;
+}
+
 lee_status cuda_fail(lee_lbm *h, cudaError_t e, const char *what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);
     if (e == cudaErrorMemoryAllocation) return fail(h, LEE_ERR_OUT_OF_MEMORY, m);
@@ -313,9 +322,14 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     h->pitch = (cells + 63) / 64 * 64;
     h->elem = elem_size(cfg->storage);
     h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
-    if (const char *ev = std::getenv("LEE_SINGLE_STEP")) h->single_step_only = ev[0] == '1';
+    if (const char *ev = std::getenv("LEE_TB_STEPS")) {
+        if (ev[0] >= '1' && ev[0] <= '4' && ev[1] == 0) h->tb_steps = ev[0] - '0';
+    }
+    if (const char *ev = std::getenv("LEE_SINGLE_STEP")) {
+        if (ev[0] == '1') h->tb_steps = 1;
+    }
     if (const char *ev = std::getenv("LEE_FORCE_SCALAR")) h->force_scalar = ev[0] == '1';
-    if (h->force_scalar) h->single_step_only = true;
+    if (h->force_scalar) h->tb_steps = 1;
     h->scale = scaled_storage(cfg->storage) ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
     const size_t bytes = state_bytes(cfg->storage, h->D, h->Q, h->pitch);
@@ -331,6 +345,9 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     }
     if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
         e = o->step2_prepare();
+    if (e == cudaSuccess && o->stepk_prepare && h->tb_steps >= 3 && cfg->bc == LEE_BC_PERIODIC &&
+        cfg->storage == LEE_STORE_F32)
+        e = o->stepk_prepare(h->tb_steps);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -455,17 +472,15 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         h->steps += n;
         return LEE_OK;
     }
-    // Periodic 2D FP32 grids whose width is a multiple of 4: two steps per launch
-    // (temporal blocking; bit-identical to two single steps).
-    const bool two = h->ops->step2 && !L.open && h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 4 == 0 &&
-                     h->cfg.ny >= 3 && !h->single_step_only;
-    const int unit = two ? 2 : 1;
+    // Periodic 2D FP32 grids whose width is a multiple of 4: several steps per launch
+    // (temporal blocking; bit-identical to single steps).
+    const int unit = fused_steps(h);
     auto launch_unit = [&](int from, cudaStream_t st) -> cudaError_t {
-        if (!two) return launch_step(from, st);
+        if (unit == 1) return launch_step(from, st);
         L.src = h->buf[from];
         L.dst = h->buf[from ^ 1];
         L.stream = st;
-        return h->ops->step2(L);
+        return unit == 2 ? h->ops->step2(L) : h->ops->stepk(L, unit);
     };
     int64_t units = n / unit;
     if (units * unit >= kGraphMinSteps) {
@@ -631,11 +646,9 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
 
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
-    const bool two = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
-                     h->cfg.nx % 4 == 0 && h->cfg.ny >= 3 && !h->single_step_only;
     const bool onchip = h->ops->onchip_1d && h->cfg.storage != LEE_STORE_SPLIT16 &&
                         2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
-    *steps = onchip ? 0 : (two ? 2 : 1);
+    *steps = onchip ? 0 : fused_steps(h);
     return LEE_OK;
 }
 

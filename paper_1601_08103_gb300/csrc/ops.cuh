@@ -39,6 +39,9 @@ struct SetOps {
     cudaError_t (*step2)(const StepLaunch &);
     // one-time set-up of the two-step kernel on the current device (outside stream capture)
     cudaError_t (*step2_prepare)();
+    // k = 3 or 4 fused steps per launch on the same grids, and its one-time set-up
+    cudaError_t (*stepk)(const StepLaunch &, int k);
+    cudaError_t (*stepk_prepare)(int k);
     // g = g^eq(fields) (fields FP64 on device)
     cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                         long long pitch, const SetConsts &k, cudaStream_t st);

@@ -203,6 +203,12 @@ struct SetImpl {
     }
     static cudaError_t step2_prepare() { return two_step_prepare<S>(); }
     static cudaError_t step2(const StepLaunch &L) { return two_step_launch<S>(L); }
+    static cudaError_t stepk_prepare(int k) {
+        return k == 3 ? kstep_prepare<S, 3>() : k == 4 ? kstep_prepare<S, 4>() : cudaErrorInvalidValue;
+    }
+    static cudaError_t stepk(const StepLaunch &L, int k) {
+        return k == 3 ? kstep_launch<S, 3>(L) : k == 4 ? kstep_launch<S, 4>(L) : cudaErrorInvalidValue;
+    }
     static cudaError_t edge_fixup(const StepLaunch &L) {
         if constexpr (S::D != 2) {
             return cudaErrorInvalidValue;
@@ -236,6 +242,8 @@ struct SetImpl {
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         o.step2 = S::D == 2 ? &step2 : nullptr;
         o.step2_prepare = S::D == 2 ? &step2_prepare : nullptr;
+        o.stepk = S::D == 2 ? &stepk : nullptr;
+        o.stepk_prepare = S::D == 2 ? &stepk_prepare : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);

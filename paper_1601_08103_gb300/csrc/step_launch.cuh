@@ -121,4 +121,68 @@ cudaError_t two_step_launch(const StepLaunch &L) {
     }
 }
 
+
+// The same for K steps per launch (K = 3, 4): resident capacity per device, then the launch.
+template <class S, int K>
+int *kstep_capacity() {
+    static int cap[64] = {0};
+    return cap;
+}
+template <class S, int K>
+cudaError_t kstep_prepare() {
+    if constexpr (S::D != 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (kstep_capacity<S, K>()[dev]) return cudaSuccess;
+        constexpr int smem = tbk_smem_bytes<S, K>();
+        e = cudaFuncSetAttribute(k_stream_collide_kstep<S, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stream_collide_kstep<S, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, per_sm_pf = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_kstep<S, K, false>, 128, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pf, k_stream_collide_kstep<S, K, true>, 128, smem);
+        if (per_sm_pf < per_sm) per_sm = per_sm_pf;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        kstep_capacity<S, K>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+        return cudaSuccess;
+    }
+}
+template <class S, int K>
+cudaError_t kstep_launch(const StepLaunch &L) {
+    if constexpr (S::D != 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (L.storage != LEE_STORE_F32 || L.open || L.nx % 4 != 0 || L.ny < 3) return cudaErrorInvalidValue;
+        const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
+        constexpr int smem = tbk_smem_bytes<S, K>();
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64 || kstep_capacity<S, K>()[dev] == 0) return cudaErrorNotReady;  // prepare first
+        // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
+        const int strips = (L.nx + kTbW - 1) / kTbW;
+        int segs = kstep_capacity<S, K>()[dev] / strips;
+        if (segs < 1) segs = 1;
+        int H = (L.ny + segs - 1) / segs;
+        H = (H + 3) / 4 * 4;
+        if (H < 16) H = 16;
+        const dim3 grid(strips, (L.ny + H - 1) / H);
+        const long long bytes = 2LL * S::Q * (long long)sizeof(float) * L.nx * L.ny;
+        auto kern = bytes <= kTbL2PrefetchMaxBytes ? k_stream_collide_kstep<S, K, true>
+                                                   : k_stream_collide_kstep<S, K, false>;
+        kern<<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src), static_cast<float *>(L.dst), L.nx, L.ny,
+                                            L.pitch, H, cf);
+        return cudaGetLastError();
+    }
+}
+
 }  // namespace lee

@@ -61,7 +61,8 @@ def test_reference_arm_contract(monkeypatch):
 def test_profiled_traffic_is_null_when_kernel_changed(tmp_path, monkeypatch):
     p = tmp_path / "prof.md"
     p.write_text("kernel_source_sha256_16: deadbeefdeadbeef\ndram_bytes_per_launch: 1.0e8\n")
-    monkeypatch.setattr(bench, "PROFILE", str(p))
-    assert bench.profiled_traffic() is None
+    monkeypatch.setattr(bench, "PROFILES", {3: str(p)})
+    assert bench.profiled_traffic(3) is None
     p.write_text(f"kernel_source_sha256_16: {bench.kernel_source_sha()}\ndram_bytes_per_launch: 1.0e8\n")
-    assert bench.profiled_traffic() == pytest.approx(1.0e8)
+    assert bench.profiled_traffic(3) == pytest.approx(1.0e8)
+    assert bench.profiled_traffic(2) is None  # no summary for that kernel

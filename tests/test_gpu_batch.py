@@ -57,6 +57,20 @@ def test_batched_modes_equal_single_domain_bitwise(gpu_lib, storage):
                 assert np.array_equal(got[d], want[d]), (storage, nsteps, mode, d)
 
 
+@pytest.mark.parametrize("fused", [1, 2, 3, 4])
+def test_batched_fused_steps_equal_single_domain_bitwise(gpu_lib, monkeypatch, fused):
+    """LEE_TB_STEPS at create time sets how many steps the batched FP32 kernel fuses per launch
+    (four by default); every choice gives each domain the bits of single steps."""
+    lee = gpu_lib
+    fields = fields_for(DOMAINS, 5)
+    want = run_single(lee, "f32", DOMAINS, 4 * fused + 3, fields)
+    monkeypatch.setenv("LEE_TB_STEPS", str(fused))
+    for mode in ("graph", "launch"):
+        got = run_batch(lee, "f32", DOMAINS, 4 * fused + 3, mode, fields)
+        for d in range(len(DOMAINS)):
+            assert np.array_equal(got[d], want[d]), (fused, mode, d)
+
+
 def test_every_launch_shape_gives_the_same_result(gpu_lib):
     lee = gpu_lib
     doms = [(nx, ny, t) for nx, ny, t in DOMAINS if nx % 4 == 0]

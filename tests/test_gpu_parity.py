@@ -313,17 +313,55 @@ def test_1d_config_matches_oracle_and_dalembert(gpu_lib):
 
 
 @pytest.mark.parametrize("name", ["D2Q5", "D2Q5_DI"])
-def test_two_step_kernel_parity(gpu_lib, name):
-    """Periodic 2D FP32 grids with nx a multiple of 4 advance two steps per launch with the
-    intermediate state in shared memory; checked against the oracle on full and partial
-    128-column strips, ragged tile rows and a grid narrower than one strip."""
+@pytest.mark.parametrize("fused", [2, 3, 4])
+def test_multi_step_kernel_parity(gpu_lib, monkeypatch, name, fused):
+    """Periodic 2D FP32 grids with nx a multiple of 4 advance several steps per launch with the
+    intermediate states in shared memory (LEE_TB_STEPS at create time picks how many; four by
+    default); checked against the oracle on full and partial 128-column strips, ragged tile rows,
+    a grid narrower than one strip and runs that end with single steps."""
     lee = gpu_lib
-    for shape in ((256, 37, 1), (260, 41, 1), (12, 5, 1)):
-        for n, tau in ((2, 0.6), (3, 0.5), (50, 0.83)):
+    monkeypatch.setenv("LEE_TB_STEPS", str(fused))
+    for shape in ((256, 37, 1), (260, 41, 1), (12, 5, 1), (384, 130, 1)):
+        for n, tau in ((fused, 0.6), (2 * fused + 1, 0.5), (50, 0.83)):
             with lee.Solver(name, shape, tau, storage="f32") as sv:
-                assert sv.steps_per_launch == 2
+                assert sv.steps_per_launch == fused
             r = run_pair(lee, name, shape, tau, n, storage="f32", seed=n + 40)
-            assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} two-step {shape} n={n}")
+            assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} {fused}-step {shape} n={n}")
+
+
+def test_default_fuses_four_steps(gpu_lib, monkeypatch):
+    lee = gpu_lib
+    monkeypatch.delenv("LEE_TB_STEPS", raising=False)
+    monkeypatch.delenv("LEE_SINGLE_STEP", raising=False)
+    with lee.Solver("D2Q5", (2048, 2048, 1), 0.6, storage="f32") as sv:
+        assert sv.steps_per_launch == 4
+    with lee.Solver("D2Q5", (2046, 64, 1), 0.6, storage="f32") as sv:  # nx not a multiple of 4
+        assert sv.steps_per_launch == 1
+    with lee.Solver("D2Q5", (256, 64, 1), 0.6, storage="f16") as sv:
+        assert sv.steps_per_launch == 1
+
+
+@pytest.mark.parametrize("fused", [2, 3, 4])
+@pytest.mark.parametrize("shape", [(256, 37, 1), (260, 41, 1), (12, 5, 1), (1024, 1000, 1), (2048, 2048, 1)])
+def test_multi_step_kernel_equals_single_steps(gpu_lib, monkeypatch, fused, shape):
+    """Every intermediate level is rounded to FP32 like a stored state, so k fused steps give
+    the bits of k single steps (runs of 3k+1 steps: graphs of fused launches plus one single
+    step), up to the 2048^2 benchmark grid."""
+    lee = gpu_lib
+    cells = int(np.prod(shape))
+    rho, u, th = inputs.random_fields(shape, 2, 29)
+    n = 3 * fused + 1 if cells < 1 << 20 else 6 * fused + 1
+    outs = []
+    for k in (1, fused):
+        monkeypatch.setenv("LEE_TB_STEPS", str(k))
+        with lee.Solver("D2Q5", shape, 0.55, storage="f32") as sv:
+            assert sv.steps_per_launch == k
+            sv.init_fields(rho, u, th)
+            sv.step(n)
+            g = np.empty((5, cells), dtype=np.float64)
+            sv.get_populations(g)
+            outs.append(g)
+    assert np.array_equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
