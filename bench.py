@@ -567,6 +567,7 @@ CASES = {
     "d2q5_f32": ("D2Q5", (2048, 2048, 1), "f32", 0.6),
     "d2q5_f64": ("D2Q5", (2048, 2048, 1), "f64", 0.6),
     "d3q7_f32": ("D3Q7", (384, 384, 384), "f32", 0.55),
+    "d3q7_f32_256": ("D3Q7", (256, 256, 256), "f32", 0.55),
     "d3q7_f64": ("D3Q7", (384, 384, 384), "f64", 0.55),
     "d3q7_f16": ("D3Q7", (384, 384, 384), "f16", 0.55),
     "d3q7_bf16": ("D3Q7", (384, 384, 384), "bf16", 0.55),

@@ -166,6 +166,8 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  *    intermediate states kept in shared memory (temporal blocking; LEE_TB_STEPS=1..4 in the
  *    environment at create time picks another count; lee_lbm_steps_per_launch reports it); a
  *    run of n steps is n / 4 such launches and n % 4 single steps;
+ *  - periodic 3D FP32 grids of D3Q7 and diatomic D3Q7 with nx a multiple of 4 advance two steps
+ *    per launch (a z-marching tile; LEE_TB_STEPS=1 keeps one step per launch);
  *  - a 1D grid whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
@@ -211,8 +213,9 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
 /* How lee_lbm_step runs this grid: *steps = 1 (one fused stream-collide launch per time step),
  * 2..4 (periodic 2D FP32 grids with nx a multiple of 4: that many time steps per launch, the
  * intermediate states kept in shared memory -- temporal blocking; 4 unless LEE_TB_STEPS was set
- * at create time) or 0 (small 1D grid: all steps of a call in one on-chip launch).  All forms
- * give bit-identical results. */
+ * at create time; periodic 3D FP32 D3Q7 and diatomic D3Q7 grids with nx a multiple of 4: 2) or
+ * 0 (small 1D grid: all steps of a call in one on-chip launch).  All forms give bit-identical
+ * results. */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);
 
 /* The 16-bit storage scale S in use (1 for F64/F32 storage). */

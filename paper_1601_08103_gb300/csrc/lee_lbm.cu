@@ -127,12 +127,20 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
     return s;
 }
 
-// Time steps fused per launch: tb_steps on periodic 2D FP32 grids whose width is a multiple of 4
-// (temporal blocking), one step otherwise.
+// Time steps fused per launch (temporal blocking): tb_steps on periodic 2D FP32 grids whose width
+// is a multiple of 4; two on periodic 3D FP32 grids of the axis-velocity sets whose width is a
+// multiple of 4; one step otherwise (16-bit storage moves half the bytes and stays on the one-step
+// kernel, which measured faster there).
+bool tiled_3d(const lee_lbm *h) {
+    return h->ops->step3d2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
+           h->cfg.nx % 4 == 0;
+}
 int fused_steps(const lee_lbm *h) {
+    if (h->tb_steps <= 1) return 1;
+    if (tiled_3d(h)) return 2;
     const bool tiled = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
                        h->cfg.nx % 4 == 0 && h->cfg.ny >= 3;
-    if (!tiled || h->tb_steps <= 1) return 1;
+    if (!tiled) return 1;
     return h->tb_steps >= 3 && h->ops->stepk ? h->tb_steps : 2;
 }
 
@@ -348,6 +356,7 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && o->stepk_prepare && h->tb_steps >= 3 && cfg->bc == LEE_BC_PERIODIC &&
         cfg->storage == LEE_STORE_F32)
         e = o->stepk_prepare(h->tb_steps);
+    if (e == cudaSuccess && h->tb_steps >= 2 && tiled_3d(h)) e = o->step3d2_prepare(cfg->storage);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -480,6 +489,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         L.src = h->buf[from];
         L.dst = h->buf[from ^ 1];
         L.stream = st;
+        if (h->D == 3) return h->ops->step3d2(L);
         return unit == 2 ? h->ops->step2(L) : h->ops->stepk(L, unit);
     };
     int64_t units = n / unit;

@@ -42,6 +42,10 @@ struct SetOps {
     // k = 3 or 4 fused steps per launch on the same grids, and its one-time set-up
     cudaError_t (*stepk)(const StepLaunch &, int k);
     cudaError_t (*stepk_prepare)(int k);
+    // two fused steps per launch for the 3D axis-velocity sets (periodic, FP32, nx % 4 == 0;
+    // nullptr for other sets), and its one-time set-up for a storage type
+    cudaError_t (*step3d2)(const StepLaunch &);
+    cudaError_t (*step3d2_prepare)(int storage);
     // g = g^eq(fields) (fields FP64 on device)
     cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                         long long pitch, const SetConsts &k, cudaStream_t st);

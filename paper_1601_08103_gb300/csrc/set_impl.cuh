@@ -4,6 +4,7 @@
 #include "onchip_cluster.cuh"
 #include "split.cuh"
 #include "step_launch.cuh"
+#include "tb3d.cuh"
 
 namespace lee {
 
@@ -209,6 +210,21 @@ struct SetImpl {
     static cudaError_t stepk(const StepLaunch &L, int k) {
         return k == 3 ? kstep_launch<S, 3>(L) : k == 4 ? kstep_launch<S, 4>(L) : cudaErrorInvalidValue;
     }
+    // two steps per launch in 3D (axis-velocity sets, FP32 storage)
+    static cudaError_t step3d2_prepare(int storage) {
+        if constexpr (!axis_only<S>()) {
+            return cudaErrorInvalidValue;
+        } else {
+            return storage == LEE_STORE_F32 ? t3_prepare<S, float, kT3Rows>() : cudaErrorInvalidValue;
+        }
+    }
+    static cudaError_t step3d2(const StepLaunch &L) {
+        if constexpr (!axis_only<S>()) {
+            return cudaErrorInvalidValue;
+        } else {
+            return L.storage == LEE_STORE_F32 ? t3_launch<S, float, kT3Rows>(L) : cudaErrorInvalidValue;
+        }
+    }
     static cudaError_t edge_fixup(const StepLaunch &L) {
         if constexpr (S::D != 2) {
             return cudaErrorInvalidValue;
@@ -244,6 +260,8 @@ struct SetImpl {
         o.step2_prepare = S::D == 2 ? &step2_prepare : nullptr;
         o.stepk = S::D == 2 ? &stepk : nullptr;
         o.stepk_prepare = S::D == 2 ? &stepk_prepare : nullptr;
+        o.step3d2 = axis_only<S>() ? &step3d2 : nullptr;
+        o.step3d2_prepare = axis_only<S>() ? &step3d2_prepare : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);

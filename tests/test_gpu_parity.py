@@ -364,6 +364,45 @@ def test_multi_step_kernel_equals_single_steps(gpu_lib, monkeypatch, fused, shap
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("name", ["D3Q7", "D3Q7_DI"])
+def test_3d_two_step_kernel_equals_single_steps(gpu_lib, monkeypatch, name):
+    """Periodic 3D FP32 grids of the axis-velocity sets advance two steps per launch (a
+    z-marching tile keeps S(t+1) in registers and a shared-memory ring), bit-identical to single
+    steps: full and partial 128-column strips, ragged tile rows and z segments, a grid one strip
+    wide, odd step counts; 16-bit storage stays on one step per launch."""
+    lee = gpu_lib
+    s = oracle.velset(name)
+    storage = "f32"
+    for st16 in ("f16", "bf16"):
+        with lee.Solver(name, (128, 10, 5), 0.55, storage=st16) as sv:
+            assert sv.steps_per_launch == 1
+    for shape in ((128, 10, 5), (132, 9, 6), (256, 13, 7), (384, 40, 24), (128, 8, 400)):
+        cells = int(np.prod(shape))
+        rho, u, th = inputs.random_fields(shape, 3, 31)
+        outs = []
+        for k in (1, 2):
+            monkeypatch.setenv("LEE_TB_STEPS", str(k))
+            with lee.Solver(name, shape, 0.55, storage=storage) as sv:
+                assert sv.steps_per_launch == k
+                sv.init_fields(rho, u, th)
+                sv.step(11)
+                g = np.empty((s.q, cells))
+                sv.get_populations(g)
+                outs.append(g)
+        assert np.array_equal(outs[0], outs[1]), shape
+
+
+@pytest.mark.parametrize("name", ["D3Q7", "D3Q7_DI"])
+def test_3d_two_step_kernel_parity(gpu_lib, name):
+    """The default 3D FP32 path (two steps per launch) against the oracle."""
+    lee = gpu_lib
+    for shape, n, tau in (((128, 10, 5), 2, 0.6), ((132, 9, 6), 7, 0.5), ((256, 13, 7), 20, 0.83)):
+        with lee.Solver(name, shape, tau, storage="f32") as sv:
+            assert sv.steps_per_launch == 2
+        r = run_pair(lee, name, shape, tau, n, storage="f32", seed=n + 60)
+        assert_close(r["g_gpu"], r["g_ora"], TOL["f32"], f"{name} 3D two-step {shape} n={n}")
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_3d_diatomic_pulse_in_dimensional_units(gpu_lib, storage):
     """The 3D diatomic run of Sec. 9.3 set up from its dimensional data: background density and
