@@ -1,7 +1,7 @@
 // step_launch.cuh -- launch configuration of the fused stream-collide kernels for one velocity set:
-// the one-step kernel (cells per thread, grid) and the two-step kernel (tile height from the
-// resident capacity).  Together with kernels.cuh and velsets.cuh this fixes what the profiled
-// hot-path launches execute.
+// the one-step kernel (cells per thread, grid) and the two-step and K-step 2D kernels (tile height
+// from the resident capacity).  Together with kernels.cuh and velsets.cuh this fixes what the
+// profiled hot-path launches execute.
 #pragma once
 
 #include "ops.cuh"

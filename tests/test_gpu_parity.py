@@ -427,7 +427,7 @@ def test_3d_diatomic_pulse_in_dimensional_units(gpu_lib, storage):
 @pytest.mark.parametrize("bc", ["periodic", "open_sponge"])
 def test_vector_and_packed_paths_equal_the_scalar_path(gpu_lib, monkeypatch, name, storage, bc):
     """The vector kernels (several cells per thread; FP32 collisions on packed f32x2 pairs; the
-    two-step kernel) spell out every rounding like the one-cell-per-thread kernel, so a run gives
+    multi-step kernels) spell out every rounding like the one-cell-per-thread kernel, so a run gives
     the same bits on both paths.  LEE_FORCE_SCALAR=1 at create time selects the scalar path."""
     lee = gpu_lib
     s = oracle.velset(name)
