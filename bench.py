@@ -36,6 +36,7 @@ SET = "D2Q5"
 STORAGE = "f32"
 BYTES_PER_LUP = 2 * 5 * 4  # read + write of q = 5 FP32 populations (algorithmic)
 L2_FLUSH_BYTES = 512 << 20
+NOMINAL_HBM_GBS = 8000.0  # HBM3e nominal bandwidth of the part (the measured copy peak is the denominator of frac)
 WORKLOAD = "2D D2Q5 periodic 2048x2048, FP32, tau=0.6, pulse+8 plane waves, 1000 steps/job"
 # ncu summary of the stream-collide kernel the benchmark runs, by time steps fused per launch
 PROFILES = {k: os.path.join(ROOT, "profiles", f"stream_collide_{k}step_d2q5_f32_2048x2048.md") for k in (1, 2, 3, 4)}
@@ -284,6 +285,9 @@ def run_ours(args, rank, world, local):
                    "wall_s_timed_region": round(wall, 3)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                     "bytes_per_update": BYTES_PER_LUP / spl,
+                     "update_bound_mlups": round(peak / (BYTES_PER_LUP / spl) * 1e3, 1),
                      "kernel": KERNEL_NAMES.get(spl, "?"),
                      "steps_per_launch": spl,
                      "launches_per_job": {"fused": NSTEPS // spl, "single_step": NSTEPS % spl},
