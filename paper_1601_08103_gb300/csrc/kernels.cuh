@@ -780,7 +780,8 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
 // ---------------------------------------------------------------------------------------------
 // K time steps per launch (deeper temporal blocking), periodic 2D FP32 grids with nx % 4 == 0
 // ---------------------------------------------------------------------------------------------
-// The two-step tile generalised to K levels (K = 4 by default, 3 on request).  Level l
+// The two-step tile generalised to K levels (K = 4 by default, 3 on request), without the L2
+// prefetch (this kernel is issue bound; the prefetch cost 3.5 % on 2048^2).  Level l
 // (1 <= l < K) is S(t+l) on rows y0-(K-l) .. y0+H-1+(K-l) and columns x0-(K-l) .. x0+127+(K-l)
 // of the tile; it lives in its own 2-slot ring of 4-row blocks (block j of level l holds rows
 // y0-(K-l)+4j .. y0-(K-l)+4j+3, one per warp).  Level K is the output tile, stored to global
@@ -800,7 +801,8 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
 // Measured on GB300 (D2Q5, GLUPS on 2048^2 / 4096^2 / 8192^2): two steps per launch 284 / 298 /
 // 290; three levels with 3-slot rings and one barrier per iteration 351 / 388 / 409; four levels
 // that way (98 KB, two blocks per SM) 352 / 392 / 365; four levels with 2-slot rings 391 / 475 /
-// 499; five levels with 2-slot rings (87 KB, two blocks per SM) 396 / 429 / 395.  The kernel is
+// 499, and 402 / 473 / 498 without the L2 prefetch; five levels with 2-slot rings (87 KB, two
+// blocks per SM) 396 / 429 / 395; four levels with two warps per row 308 / 384 / 401.  The kernel is
 // bound by instruction issue and latency, not DRAM (ncu: issue slots half busy, 12 warps per
 // SM), so the level count that keeps three blocks resident wins.  Giving each level's halo cells
 // of all four rows to one warp (4x fewer halo collisions) lost 5-18 %: the barriers then wait
@@ -814,7 +816,7 @@ constexpr int tbk_min_blocks() {
     return K == 3 ? 5 : 3;
 }
 
-template <class S, int K, bool PF>
+template <class S, int K>
 __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
                                          long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
                                          float *smem) {
@@ -875,16 +877,6 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
         }
         rn += 4;
         while (rn >= ny) rn -= ny;
-        if constexpr (PF) {
-            if ((lane & 7) == 0 && a + 4 <= lim1) {
-                const int rows2[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};
-                static_for<Q>([&](auto I) {
-                    constexpr int i = decltype(I)::value;
-                    constexpr int cy = S::c(i, 1);
-                    prefetch_l2(src + (long long)i * pitch + (long long)rows2[1 - cy] * nx + xa);
-                });
-            }
-        }
     };
     load_a(0);
 
@@ -977,13 +969,13 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     }
 }
 
-template <class S, int K, bool PF>
+template <class S, int K>
 __global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kstep(const float *__restrict__ src,
                                                                                 float *__restrict__ dst, int nx,
                                                                                 int ny, long long pitch, int H,
                                                                                 CollideCoef<float> cf) {
     extern __shared__ __align__(16) float tb_smem[];
-    tbk_tile<S, K, PF>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
+    tbk_tile<S, K>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
 }
 
 // K fused steps over many periodic domains: block b works on tile tiles[b] = (domain, x0, y0)
@@ -995,7 +987,7 @@ __global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kst
     extern __shared__ __align__(16) float tb_smem[];
     const int3 tl = tiles[blockIdx.x];
     const TbDomain &D = doms[tl.x];
-    tbk_tile<S, K, false>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
+    tbk_tile<S, K>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
 }
 
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the
