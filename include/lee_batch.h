@@ -49,7 +49,7 @@ lee_status lee_batch_init_fields(lee_batch *b, int32_t d, const double *rho, con
  * mode a run of up to 4096 steps is one launch of a graph holding all its steps (captured on
  * first use of that length and parity, then cached); longer runs replay a 100-step graph.  With
  * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance four steps per
- * launch (the intermediate states kept in shared memory; tiles of 128 columns x up to 128 rows,
+ * launch (the intermediate states kept in shared memory; tiles of 128 columns x up to 64 rows,
  * dispatched largest first; LEE_TB_STEPS=1..4 in the environment at create time picks another
  * count), bit-identical to single steps. */
 lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode);

@@ -293,8 +293,10 @@ lee_status tune(lee_batch *b) {
 }
 
 // Multi-step tiles of 128 columns x at most kBatchTileRows rows (fewer for short domains),
-// listed largest first so that the block scheduler balances the uneven domains.
-constexpr int kBatchTileRows = 128;
+// listed largest first so that the block scheduler balances the uneven domains.  Measured on
+// GB300 with the four-step kernel on the 96-domain workload (sides multiples of 64): 64 rows 374
+// GLUPS, 48 / 56 / 72 / 80 rows 360-366, 128 rows 367, 256 rows 359.
+constexpr int kBatchTileRows = 64;
 
 lee_status build_tb(lee_batch *b, int unit) {
     cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_tb<D2Q5>(unit, &b->tb_fn)
