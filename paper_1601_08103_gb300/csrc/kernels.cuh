@@ -802,7 +802,11 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
 // 290; three levels with 3-slot rings and one barrier per iteration 351 / 388 / 409; four levels
 // that way (98 KB, two blocks per SM) 352 / 392 / 365; four levels with 2-slot rings 391 / 475 /
 // 499, and 402 / 473 / 498 without the L2 prefetch; five levels with 2-slot rings (87 KB, two
-// blocks per SM) 396 / 429 / 395; four levels with two warps per row 308 / 384 / 401.  The kernel is
+// blocks per SM) 396 / 429 / 395; four levels with two warps per row 308 / 384 / 401.  Integer
+// work is about as large as the floating-point work here, so the ring is addressed as an 8-row
+// circular buffer per level (410 / 480 / 505) and the iteration loop is unrolled by two with the
+// parity known at compile time, which makes every buffer row a per-thread constant
+// (419 / 491 / 517).  The kernel is
 // bound by instruction issue and latency, not DRAM (ncu: issue slots half busy, 12 warps per
 // SM), so the level count that keeps three blocks resident wins.  Giving each level's halo cells
 // of all four rows to one warp (4x fewer halo collisions) lost 5-18 %: the barriers then wait
@@ -822,10 +826,10 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
                                          float *smem) {
     static_assert(S::D == 2 && K >= 3 && K <= 4, "deep tiles are 2D with three or four levels");
     constexpr int Q = S::Q;
-    // row of level l (1 .. K-1), ring block blk, warp row w, velocity i; column x0 at offset 4
-    auto ring = [&](int l, int blk, int w, int i) {
-        return smem + ((((l - 1) * 2 + (blk & 1)) * 4 + w) * Q + i) * kTbRow;
-    };
+    // The two 4-row slots of level l (1 .. K-1) form an 8-row circular buffer: row rr of the
+    // level (counted from its first row) lives in buffer row rr & 7.  ring(l, r8) is velocity 0
+    // of that row (velocity i at + i * kTbRow), column x0 at offset 4.
+    auto ring = [&](int l, int r8) { return smem + ((l - 1) * 8 + r8) * Q * kTbRow; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int iters = H / 4 + K - 1;
     auto wrap_x = [&](int x) {
@@ -880,28 +884,37 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     };
     load_a(0);
 
-    // level l >= 2 (or K), block j: the lane's cells pulled from blocks j, j+1 of level l-1
-    auto pull_level = [&](int l, int j, float (&pb)[Q][kTbV]) {
+    // level l >= 2 (or K), row 4j + warp: velocity i is pulled from row 4j + warp + 1 - c_y of
+    // level l-1 (whose rows start one earlier); rows[1 - c_y] points at those three rows.  JP is
+    // the parity of j, known at compile time (the iteration loop is unrolled by two), so the
+    // buffer rows are per-thread constants.
+    auto src_rows = [&](int l, auto JP, const float *(&rows)[3]) {
+        constexpr int jp = decltype(JP)::value;
+        rows[0] = ring(l - 1, (4 * jp + warp) & 7);
+        rows[1] = ring(l - 1, (4 * jp + warp + 1) & 7);
+        rows[2] = ring(l - 1, (4 * jp + warp + 2) & 7);
+    };
+    auto pull_level = [&](const float *const (&rows)[3], float (&pb)[Q][kTbV]) {
         static_for<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-            const int rr = 4 * j + warp + 1 - cy;  // row within the blocks of level l-1
-            tb_pull<cx>(ring(l - 1, rr >> 2, rr & 3, i), lane, pb[i]);
+            tb_pull<cx>(rows[1 - cy] + i * kTbRow, lane, pb[i]);
         });
     };
-    // level l >= 2, block j: the halo cell at offset o, pulled from level l-1
-    auto pull_halo = [&](int l, int j, int o, float (&hin)[Q][1]) {
+    // the halo cell at offset o, pulled from level l-1
+    auto pull_halo = [&](const float *const (&rows)[3], int o, float (&hin)[Q][1]) {
         static_for<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-            const int rr = 4 * j + warp + 1 - cy;
-            hin[i][0] = ring(l - 1, rr >> 2, rr & 3, i)[4 + o - cx];
+            hin[i][0] = rows[1 - cy][i * kTbRow + 4 + o - cx];
         });
     };
 
-    for (int k = 0; k < iters; ++k) {
-        // level 1, block k
-        if (y0 - (K - 1) + 4 * k + warp <= lim1) {  // warp-uniform
+    // iteration k; KP = k & 1 at compile time
+    auto iteration = [&](int k, auto KP) {
+        constexpr int kp = decltype(KP)::value;
+        // level 1, row 4k + warp (rows of level l run to H - 1 + 2 (K - l) in that count)
+        if (4 * k + warp <= H - 1 + 2 * (K - 1)) {  // warp-uniform
             float pa[Q][kTbV];
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
@@ -925,39 +938,46 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
             float post[Q][kTbV], hout[Q][1];
             collide_chunk<S, kTbPacked>(pa, post, cf);
             collide_chunk<S, kTbPacked>(hin, hout, cf);
+            float *dst1 = ring(1, 4 * kp + warp);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) tb_st(ring(1, k, warp, i) + kTbV * lane + 4, post[i]);
+            for (int i = 0; i < Q; ++i) tb_st(dst1 + i * kTbRow + kTbV * lane + 4, post[i]);
             if (lane < 2 * (K - 1)) {
                 const int o = hoff(K - 1);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) ring(1, k, warp, i)[4 + o] = hout[i][0];
+                for (int i = 0; i < Q; ++i) dst1[i * kTbRow + 4 + o] = hout[i][0];
             }
         }
         if (k + 1 < iters) load_a(k + 1);
         __syncthreads();  // level-1 block k visible; every read of the slots written below is done
         static_for<K - 2>([&](auto Lx) {
             constexpr int l = 2 + decltype(Lx)::value;
+            constexpr int jp = (kp - (l - 1)) & 1;
             const int j = k - (l - 1);
-            if (j >= 0 && y0 - (K - l) + 4 * j + warp <= y0 + H - 1 + (K - l)) {  // warp-uniform
+            if (j >= 0 && 4 * j + warp <= H - 1 + 2 * (K - l)) {  // warp-uniform
                 const int o = hoff(K - l);
+                const float *rows[3];
+                src_rows(l, std::integral_constant<int, jp>{}, rows);
                 float pb[Q][kTbV], post[Q][kTbV], hin[Q][1], hout[Q][1];
-                pull_level(l, j, pb);
-                pull_halo(l, j, o, hin);
+                pull_level(rows, pb);
+                pull_halo(rows, o, hin);
                 collide_chunk<S, kTbPacked>(pb, post, cf);
                 collide_chunk<S, kTbPacked>(hin, hout, cf);
+                float *dstl = ring(l, 4 * jp + warp);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) tb_st(ring(l, j, warp, i) + kTbV * lane + 4, post[i]);
+                for (int i = 0; i < Q; ++i) tb_st(dstl + i * kTbRow + kTbV * lane + 4, post[i]);
                 if (lane < 2 * (K - l)) {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) ring(l, j, warp, i)[4 + o] = hout[i][0];
+                    for (int i = 0; i < Q; ++i) dstl[i * kTbRow + 4 + o] = hout[i][0];
                 }
             }
             __syncthreads();  // level l block j visible to level l+1
         });
         const int m = k - (K - 1);
         if (m >= 0) {
+            const float *rows[3];
+            src_rows(K, std::integral_constant<int, (kp - (K - 1)) & 1>{}, rows);
             float pb[Q][kTbV], post[Q][kTbV];
-            pull_level(K, m, pb);
+            pull_level(rows, pb);
             collide_chunk<S, kTbPacked>(pb, post, cf);
             const int d = y0 + 4 * m + warp;
             if (d < ny && x0 + kTbV * lane < nx) {
@@ -966,7 +986,13 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
                 for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
             }
         }
+    };
+    int k = 0;
+    for (; k + 1 < iters; k += 2) {
+        iteration(k, std::integral_constant<int, 0>{});
+        iteration(k + 1, std::integral_constant<int, 1>{});
     }
+    if (k < iters) iteration(k, std::integral_constant<int, 0>{});
 }
 
 template <class S, int K>
