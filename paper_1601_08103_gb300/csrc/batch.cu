@@ -52,7 +52,7 @@ cudaError_t launch_batched_2step(const void *src, void *dst, const void *doms, c
 template <class S, int K>
 cudaError_t launch_batched_kstep(const void *src, void *dst, const void *doms, const void *tiles, int nblocks,
                                  cudaStream_t st) {
-    k_stream_collide_kstep_batched<S, K><<<nblocks, 128, tbk_smem_bytes<S, K>(), st>>>(
+    k_stream_collide_kstep_batched<S, K><<<nblocks, kTbkThreads, tbk_smem_bytes<S, K>(), st>>>(
         static_cast<const float *>(src), static_cast<float *>(dst), static_cast<const TbDomain *>(doms),
         static_cast<const int3 *>(tiles));
     return cudaGetLastError();

@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
 // prefetch (this kernel is issue bound; the prefetch cost 3.5 % on 2048^2).  Level l
 // (1 <= l < K) is S(t+l) on rows y0-(K-l) .. y0+H-1+(K-l) and columns x0-(K-l) .. x0+127+(K-l)
 // of the tile; it lives in its own 2-slot ring of 4-row blocks (block j of level l holds rows
-// y0-(K-l)+4j .. y0-(K-l)+4j+3, one per warp).  Level K is the output tile, stored to global
+// y0-(K-l)+4j .. y0-(K-l)+4j+3, one per row warp).  Level K is the output tile, stored to global
 // memory.  Iteration k runs
 //   level 1, block k: pulled from S(t) in global memory (loads issued one iteration ahead);
 //   barrier;
@@ -793,31 +793,33 @@ __global__ void __launch_bounds__(128, kTbMinBlocks) k_stream_collide_2step_batc
 // Level l, block j reads blocks j+1 (written in the interval just before) and j (one iteration
 // earlier) of level l-1, and overwrites the slot of its own block j-2, which level l+1 last read
 // one iteration earlier; so two slots per ring suffice with one barrier per level: K-1 barriers
-// per iteration and H/4 + K - 1 iterations per tile.  The K-l halo columns on each side of level l belong to lanes
-// 0 .. 2(K-l)-1, one cell each.  Every level is rounded to FP32 exactly like a stored state, so
-// the result equals K single steps bit for bit.  Shared memory: K-1 rings of 2 x 4 x q x (128+8)
-// floats, 65.3 KB for four levels of D2Q5 (three blocks = 12 warps per SM).
+// per iteration and H/4 + K - 1 iterations per tile.  A block has four row warps (128 columns of
+// one row each) and a fifth warp for the K-l halo columns on each side of every level l < K, for
+// all four rows at once.  Every level is rounded to FP32 exactly like a stored state, so the
+// result equals K single steps bit for bit.  Shared memory: K-1 rings of 2 x 4 x q x (128+8)
+// floats, 65.3 KB for four levels of D2Q5 (three blocks = 15 warps per SM).
 //
 // Measured on GB300 (D2Q5, GLUPS on 2048^2 / 4096^2 / 8192^2): two steps per launch 284 / 298 /
 // 290; three levels with 3-slot rings and one barrier per iteration 351 / 388 / 409; four levels
-// that way (98 KB, two blocks per SM) 352 / 392 / 365; four levels with 2-slot rings 391 / 475 /
-// 499, and 402 / 473 / 498 without the L2 prefetch; five levels with 2-slot rings (87 KB, two
-// blocks per SM) 396 / 429 / 395; four levels with two warps per row 308 / 384 / 401.  Integer
-// work is about as large as the floating-point work here, so the ring is addressed as an 8-row
-// circular buffer per level (410 / 480 / 505) and the iteration loop is unrolled by two with the
-// parity known at compile time, which makes every buffer row a per-thread constant
-// (419 / 491 / 517).  The kernel is
-// bound by instruction issue and latency, not DRAM (ncu: issue slots half busy, 12 warps per
-// SM), so the level count that keeps three blocks resident wins.  Giving each level's halo cells
-// of all four rows to one warp (4x fewer halo collisions) lost 5-18 %: the barriers then wait
-// for that warp.
+// that way (98 KB, two blocks per SM) 352 / 392 / 365; four levels with 2-slot rings and the halo
+// cells in each row warp 391 / 475 / 499, and 402 / 473 / 498 without the L2 prefetch; five levels
+// (87 KB, two blocks per SM) 396 / 429 / 395; two warps per row 308 / 384 / 401.  Integer work is
+// about as large as the floating-point work here, so the ring is addressed as an 8-row circular
+// buffer per level (410 / 480 / 505) and the iteration loop is unrolled by two with the parity
+// known at compile time, which makes every buffer row a per-thread constant (419 / 491 / 517);
+// the fifth warp for the halo cells then takes a scalar collision per level off each row warp
+// (426 / 498 / 525).  Giving the halo cells to one of the four row warps instead lost 5-18 %: the
+// barriers then wait for that warp.  The kernel is bound by instruction issue and latency, not
+// DRAM (ncu: issue slots half busy), so the level count that keeps three blocks resident wins.
 template <class S, int K>
 constexpr int tbk_smem_bytes() {
     return (K - 1) * 2 * 4 * S::Q * kTbRow * (int)sizeof(float);
 }
+constexpr int kTbRows = 4;                       // row warps per block
+constexpr int kTbkThreads = (kTbRows + 1) * 32;  // plus the halo warp
 template <int K>
 constexpr int tbk_min_blocks() {
-    return K == 3 ? 5 : 3;
+    return K == 3 ? 4 : 3;
 }
 
 template <class S, int K>
@@ -831,6 +833,10 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     // of that row (velocity i at + i * kTbRow), column x0 at offset 4.
     auto ring = [&](int l, int r8) { return smem + ((l - 1) * 8 + r8) * Q * kTbRow; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Warps 0..3 compute the 128 columns of one row each; warp 4 computes the halo cells of all
+    // four rows (h = K - l columns on each side at level l): lane L takes cell c = L mod 8h, on
+    // row c / 2h of the block at offset hoff(h) from x0, and lanes L < 8h store it.
+    const bool halo_warp = warp == kTbRows;
     const int iters = H / 4 + K - 1;
     auto wrap_x = [&](int x) {
         x %= nx;
@@ -840,43 +846,46 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     // the element a lane's float4 lacks: column x0-1 for lane 0 (c_x = +1), x0+128 for lane 31
     // (c_x = -1)
     const int xedge = wrap_x(lane == 0 ? x0 - 1 : x0 + kTbW);
-    // Halo cells of a level with h halo columns per side: lane L < 2h owns the cell at offset
-    // hoff(h) from x0.  Every lane computes the cell of lane L mod 2h (the same columns, so the
-    // loads coalesce) and only lanes L < 2h store it: the halo work has no branch and its
-    // collision interleaves with the main one.
+    auto hrow = [&](int h) { return (lane % (8 * h)) / (2 * h); };
     auto hoff = [&](int h) {
-        const int idx = lane % (2 * h);
-        return idx < h ? idx - h : kTbW + idx - h;
+        const int c = (lane % (8 * h)) % (2 * h);
+        return c < h ? c - h : kTbW + c - h;
     };
-    // level 1 (h = K-1): the halo cell pulls velocity i from column x0 + o - c_x = xh[1 - c_x]
+    constexpr int h1 = K - 1;
+    const int w1 = halo_warp ? hrow(h1) : warp;  // the block row of this lane's level-1 work
+    const int o1 = hoff(h1);
+    // a level-1 halo cell pulls velocity i from column x0 + o1 - c_x = xh[1 - c_x]
     int xh[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) xh[e] = wrap_x(x0 + hoff(K - 1) - 1 + e);
+    for (int e = 0; e < 3; ++e) xh[e] = wrap_x(x0 + o1 - 1 + e);
 
     struct Pre {
-        float4 t[Q];     // the lane's four cells of velocity i from row a - c_y
-        float edge[Q];   // lanes 0 and 31: the element the float4 lacks
-        float halo[Q];   // the level-1 halo cell's pull of velocity i
+        float4 t[Q];     // row warps: the lane's four cells of velocity i from row a - c_y
+        float edge[Q];   // row warps, lanes 0 and 31: the element the float4 lacks
+        float halo[Q];   // halo warp: the level-1 halo cell's pull of velocity i
     };
     Pre pre;
     const int lim1 = y0 + H + K - 2;  // last level-1 row the tile needs
-    int rn = (y0 - (K - 1) + warp) % ny;
+    int rn = (y0 - (K - 1) + w1) % ny;
     if (rn < 0) rn += ny;
     auto load_a = [&](int k) {  // called once for each k = 0, 1, 2, ... in this order
-        const int a = y0 - (K - 1) + 4 * k + warp;
+        const int a = y0 - (K - 1) + 4 * k + w1;
         if (a <= lim1) {
             const int rows[3] = {rn == 0 ? ny - 1 : rn - 1, rn, rn + 1 == ny ? 0 : rn + 1};  // a-1, a, a+1
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
                 const float *rowp = src + (long long)i * pitch + (long long)rows[1 - cy] * nx;
-                pre.t[i] = __ldg(reinterpret_cast<const float4 *>(rowp + xa));
-                if constexpr (cx == 1) {
-                    if (lane == 0) pre.edge[i] = __ldg(rowp + xedge);
-                } else if constexpr (cx == -1) {
-                    if (lane == 31) pre.edge[i] = __ldg(rowp + xedge);
+                if (!halo_warp) {
+                    pre.t[i] = __ldg(reinterpret_cast<const float4 *>(rowp + xa));
+                    if constexpr (cx == 1) {
+                        if (lane == 0) pre.edge[i] = __ldg(rowp + xedge);
+                    } else if constexpr (cx == -1) {
+                        if (lane == 31) pre.edge[i] = __ldg(rowp + xedge);
+                    }
+                } else {
+                    pre.halo[i] = __ldg(rowp + xh[1 - cx]);
                 }
-                pre.halo[i] = __ldg(rowp + xh[1 - cx]);
             });
         }
         rn += 4;
@@ -884,15 +893,15 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     };
     load_a(0);
 
-    // level l >= 2 (or K), row 4j + warp: velocity i is pulled from row 4j + warp + 1 - c_y of
-    // level l-1 (whose rows start one earlier); rows[1 - c_y] points at those three rows.  JP is
-    // the parity of j, known at compile time (the iteration loop is unrolled by two), so the
+    // level l >= 2 (or K), block row w of block j: velocity i is pulled from row 4j + w + 1 - c_y
+    // of level l-1 (whose rows start one earlier); rows[1 - c_y] points at those three rows.  JP
+    // is the parity of j, known at compile time (the iteration loop is unrolled by two), so the
     // buffer rows are per-thread constants.
-    auto src_rows = [&](int l, auto JP, const float *(&rows)[3]) {
+    auto src_rows = [&](int l, auto JP, int w, const float *(&rows)[3]) {
         constexpr int jp = decltype(JP)::value;
-        rows[0] = ring(l - 1, (4 * jp + warp) & 7);
-        rows[1] = ring(l - 1, (4 * jp + warp + 1) & 7);
-        rows[2] = ring(l - 1, (4 * jp + warp + 2) & 7);
+        rows[0] = ring(l - 1, (4 * jp + w) & 7);
+        rows[1] = ring(l - 1, (4 * jp + w + 1) & 7);
+        rows[2] = ring(l - 1, (4 * jp + w + 2) & 7);
     };
     auto pull_level = [&](const float *const (&rows)[3], float (&pb)[Q][kTbV]) {
         static_for<Q>([&](auto I) {
@@ -910,72 +919,86 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
         });
     };
 
-    // iteration k; KP = k & 1 at compile time
+    // iteration k; KP = k & 1 at compile time.  The conditions on rows are uniform in the row
+    // warps (which shuffle) and per lane in the halo warp (which does not).
     auto iteration = [&](int k, auto KP) {
         constexpr int kp = decltype(KP)::value;
-        // level 1, row 4k + warp (rows of level l run to H - 1 + 2 (K - l) in that count)
-        if (4 * k + warp <= H - 1 + 2 * (K - 1)) {  // warp-uniform
-            float pa[Q][kTbV];
-            static_for<Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = S::c(i, 0);
-                const float4 t = pre.t[i];
-                if constexpr (cx == 0) {
-                    pa[i][0] = t.x; pa[i][1] = t.y; pa[i][2] = t.z; pa[i][3] = t.w;
-                } else if constexpr (cx == 1) {
-                    float left = __shfl_up_sync(kFull, t.w, 1);
-                    if (lane == 0) left = pre.edge[i];
-                    pa[i][0] = left; pa[i][1] = t.x; pa[i][2] = t.y; pa[i][3] = t.z;
-                } else {
-                    float right = __shfl_down_sync(kFull, t.x, 1);
-                    if (lane == 31) right = pre.edge[i];
-                    pa[i][0] = t.y; pa[i][1] = t.z; pa[i][2] = t.w; pa[i][3] = right;
-                }
-            });
-            float hin[Q][1];
+        // level 1, row 4k + w (rows of level l run to H - 1 + 2 (K - l) in that count)
+        if (!halo_warp) {
+            if (4 * k + warp <= H - 1 + 2 * (K - 1)) {
+                float pa[Q][kTbV];
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cx = S::c(i, 0);
+                    const float4 t = pre.t[i];
+                    if constexpr (cx == 0) {
+                        pa[i][0] = t.x; pa[i][1] = t.y; pa[i][2] = t.z; pa[i][3] = t.w;
+                    } else if constexpr (cx == 1) {
+                        float left = __shfl_up_sync(kFull, t.w, 1);
+                        if (lane == 0) left = pre.edge[i];
+                        pa[i][0] = left; pa[i][1] = t.x; pa[i][2] = t.y; pa[i][3] = t.z;
+                    } else {
+                        float right = __shfl_down_sync(kFull, t.x, 1);
+                        if (lane == 31) right = pre.edge[i];
+                        pa[i][0] = t.y; pa[i][1] = t.z; pa[i][2] = t.w; pa[i][3] = right;
+                    }
+                });
+                float post[Q][kTbV];
+                collide_chunk<S, kTbPacked>(pa, post, cf);
+                float *dst1 = ring(1, 4 * kp + warp);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) tb_st(dst1 + i * kTbRow + kTbV * lane + 4, post[i]);
+            }
+        } else if (4 * k + w1 <= H - 1 + 2 * (K - 1)) {
+            float hin[Q][1], hout[Q][1];
 #pragma unroll
             for (int i = 0; i < Q; ++i) hin[i][0] = pre.halo[i];
-            float post[Q][kTbV], hout[Q][1];
-            collide_chunk<S, kTbPacked>(pa, post, cf);
             collide_chunk<S, kTbPacked>(hin, hout, cf);
-            float *dst1 = ring(1, 4 * kp + warp);
+            if (lane < 8 * h1) {
+                float *dst1 = ring(1, (4 * kp + w1) & 7);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) tb_st(dst1 + i * kTbRow + kTbV * lane + 4, post[i]);
-            if (lane < 2 * (K - 1)) {
-                const int o = hoff(K - 1);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) dst1[i * kTbRow + 4 + o] = hout[i][0];
+                for (int i = 0; i < Q; ++i) dst1[i * kTbRow + 4 + o1] = hout[i][0];
             }
         }
         if (k + 1 < iters) load_a(k + 1);
         __syncthreads();  // level-1 block k visible; every read of the slots written below is done
         static_for<K - 2>([&](auto Lx) {
             constexpr int l = 2 + decltype(Lx)::value;
+            constexpr int h = K - l;
             constexpr int jp = (kp - (l - 1)) & 1;
             const int j = k - (l - 1);
-            if (j >= 0 && 4 * j + warp <= H - 1 + 2 * (K - l)) {  // warp-uniform
-                const int o = hoff(K - l);
-                const float *rows[3];
-                src_rows(l, std::integral_constant<int, jp>{}, rows);
-                float pb[Q][kTbV], post[Q][kTbV], hin[Q][1], hout[Q][1];
-                pull_level(rows, pb);
-                pull_halo(rows, o, hin);
-                collide_chunk<S, kTbPacked>(pb, post, cf);
-                collide_chunk<S, kTbPacked>(hin, hout, cf);
-                float *dstl = ring(l, 4 * jp + warp);
+            if (!halo_warp) {
+                if (j >= 0 && 4 * j + warp <= H - 1 + 2 * (K - l)) {
+                    const float *rows[3];
+                    src_rows(l, std::integral_constant<int, jp>{}, warp, rows);
+                    float pb[Q][kTbV], post[Q][kTbV];
+                    pull_level(rows, pb);
+                    collide_chunk<S, kTbPacked>(pb, post, cf);
+                    float *dstl = ring(l, 4 * jp + warp);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) tb_st(dstl + i * kTbRow + kTbV * lane + 4, post[i]);
-                if (lane < 2 * (K - l)) {
+                    for (int i = 0; i < Q; ++i) tb_st(dstl + i * kTbRow + kTbV * lane + 4, post[i]);
+                }
+            } else {
+                const int wh = hrow(h), o = hoff(h);
+                if (j >= 0 && 4 * j + wh <= H - 1 + 2 * (K - l)) {
+                    const float *rows[3];
+                    src_rows(l, std::integral_constant<int, jp>{}, wh, rows);
+                    float hin[Q][1], hout[Q][1];
+                    pull_halo(rows, o, hin);
+                    collide_chunk<S, kTbPacked>(hin, hout, cf);
+                    if (lane < 8 * h) {
+                        float *dstl = ring(l, (4 * jp + wh) & 7);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) dstl[i * kTbRow + 4 + o] = hout[i][0];
+                        for (int i = 0; i < Q; ++i) dstl[i * kTbRow + 4 + o] = hout[i][0];
+                    }
                 }
             }
             __syncthreads();  // level l block j visible to level l+1
         });
         const int m = k - (K - 1);
-        if (m >= 0) {
+        if (!halo_warp && m >= 0) {
             const float *rows[3];
-            src_rows(K, std::integral_constant<int, (kp - (K - 1)) & 1>{}, rows);
+            src_rows(K, std::integral_constant<int, (kp - (K - 1)) & 1>{}, warp, rows);
             float pb[Q][kTbV], post[Q][kTbV];
             pull_level(rows, pb);
             collide_chunk<S, kTbPacked>(pb, post, cf);
@@ -996,7 +1019,7 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
 }
 
 template <class S, int K>
-__global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kstep(const float *__restrict__ src,
+__global__ void __launch_bounds__(kTbkThreads, tbk_min_blocks<K>()) k_stream_collide_kstep(const float *__restrict__ src,
                                                                                 float *__restrict__ dst, int nx,
                                                                                 int ny, long long pitch, int H,
                                                                                 CollideCoef<float> cf) {
@@ -1007,7 +1030,7 @@ __global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kst
 // K fused steps over many periodic domains: block b works on tile tiles[b] = (domain, x0, y0)
 // of height doms[domain].H, exactly as the two-step batched kernel.
 template <class S, int K>
-__global__ void __launch_bounds__(128, tbk_min_blocks<K>()) k_stream_collide_kstep_batched(
+__global__ void __launch_bounds__(kTbkThreads, tbk_min_blocks<K>()) k_stream_collide_kstep_batched(
     const float *__restrict__ src, float *__restrict__ dst, const TbDomain *__restrict__ doms,
     const int3 *__restrict__ tiles) {
     extern __shared__ __align__(16) float tb_smem[];

@@ -143,7 +143,7 @@ cudaError_t kstep_prepare() {
                                  smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_kstep<S, K>, 128, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_kstep<S, K>, kTbkThreads, smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         kstep_capacity<S, K>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
@@ -173,7 +173,7 @@ cudaError_t kstep_launch(const StepLaunch &L) {
         // No L2 prefetch: it helps the byte-bound two-step kernel on small grids, but this kernel
         // is bound by instruction issue, and the prefetch instructions cost more than they save
         // (measured on GB300, D2Q5 2048^2: 402 GLUPS without, 388 with).
-        k_stream_collide_kstep<S, K><<<grid, 128, smem, L.stream>>>(static_cast<const float *>(L.src),
+        k_stream_collide_kstep<S, K><<<grid, kTbkThreads, smem, L.stream>>>(static_cast<const float *>(L.src),
                                                                      static_cast<float *>(L.dst), L.nx, L.ny, L.pitch,
                                                                      H, cf);
         return cudaGetLastError();
