@@ -24,6 +24,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -38,6 +39,7 @@ BYTES_PER_LUP = 2 * 5 * 4  # read + write of q = 5 FP32 populations (algorithmic
 L2_FLUSH_BYTES = 512 << 20
 NOMINAL_HBM_GBS = 8000.0  # HBM3e nominal bandwidth of the part (the measured copy peak is the denominator of frac)
 WORKLOAD = "2D D2Q5 periodic 2048x2048, FP32, tau=0.6, pulse+8 plane waves, 1000 steps/job"
+METRIC = "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline"
 # ncu summary of the stream-collide kernel the benchmark runs, by time steps fused per launch
 PROFILES = {k: os.path.join(ROOT, "profiles", f"stream_collide_{k}step_d2q5_f32_2048x2048.md") for k in (1, 2, 3, 4)}
 KERNEL_NAMES = {1: "k_stream_collide<D2Q5,float,V=4,periodic>", 2: "k_stream_collide_2step<D2Q5,float>",
@@ -84,14 +86,20 @@ class ClockSampler:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, path: str | None = None):
+        """Samples go to `path` (kept), or to a temporary file removed after stop()."""
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.keep = path is not None
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix=f"lee_clocks_rank{index}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
@@ -118,7 +126,11 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         rows = []
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        if not self.keep:
+            os.unlink(self.path)
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -173,6 +185,13 @@ def barrier(world: int):
         dist.barrier()
 
 
+def bench_config(world: int) -> dict:
+    """The workload description both arms print (identical, so the two lines compare)."""
+    return {"workload": WORKLOAD, "cells": NX * NX, "lbm_steps_per_job": NSTEPS, "velset": SET, "tau": TAU,
+            "storage": STORAGE, "parallelism": f"replicas{world}",
+            "l2": "512 MiB write between timed steps; ping-pong working set 168 MB > 129 MB L2"}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -192,7 +211,7 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sv = lee.Solver(SET, (NX, NX, 1), TAU, storage=STORAGE, stream=stream)
 
-    # steps per stream-collide launch: 3 for this periodic 2D FP32 grid (three fused time steps
+    # steps per stream-collide launch: 4 for this periodic 2D FP32 grid (four fused time steps
     # per launch, the intermediate states in shared memory), 1 for the one-step kernel.  A job of
     # NSTEPS steps is NSTEPS // spl fused launches and NSTEPS % spl single steps; every launch reads
     # and writes the whole state once, so each moves the same algorithmic bytes.
@@ -217,7 +236,7 @@ def run_ours(args, rank, world, local):
         one_step(warm)
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_out.replace("{rank}", str(rank)) if args.clocks_out else None)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -267,7 +286,7 @@ def run_ours(args, rank, world, local):
     achieved = BYTES_PER_LUP * cells / kernel_avg_s / 1e9
     traffic = profiled_traffic(spl)
     line = {
-        "metric": "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline",
+        "metric": METRIC,
         "value": round(value, 1),
         "unit": "MLUPS",
         "n_gpus": world,
@@ -279,10 +298,8 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": cells, "lbm_steps_per_job": NSTEPS, "velset": SET, "tau": TAU,
-                   "storage": STORAGE, "parallelism": f"replicas{world}",
-                   "l2": "512 MiB write between timed steps; ping-pong working set 168 MB > 129 MB L2",
-                   "wall_s_timed_region": round(wall, 3)},
+        "config": bench_config(world),
+        "wall_s_timed_region": round(wall, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                      "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
@@ -298,36 +315,52 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     sv.close()
-    return line
+    # rho' of the last timed job (init, 1000 steps, moments: the same bits every job)
+    return line, mom_d[0].cpu().numpy()
 
 
-def cpu_baseline(budget_s: float = 12.0):
-    """The FP64 oracle as it stands, on all host cores, on a bounded sample of the workload:
-    the full 2048^2 grid for as many steps as fit in about budget_s seconds."""
+def cpu_baseline(max_s: float = 90.0):
+    """The FP64 oracle as it stands, on all host cores, on the benchmark job itself: init, the
+    1000 steps of the 2048^2 grid and rho' (about 22 s on 16 Grace cores).  Returns the timing
+    line and the oracle's rho', or None for rho' if the host is so slow that the job would take
+    more than max_s seconds (then a bounded number of steps is timed instead)."""
     import oracle
     from paper_1601_08103_gb300 import inputs
 
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     rho, u, th = inputs.config_2d(NX, seed=2)
-    g = oracle.equilibrium(SET, rho, u, th)
+    g0 = oracle.equilibrium(SET, rho, u, th)
     t0 = time.perf_counter()
-    g = oracle.step(SET, (NX, NX, 1), TAU, g, 2)
-    probe = time.perf_counter() - t0
-    n = int(max(2, min(200, budget_s / max(probe / 2, 1e-6))))
+    g = oracle.step(SET, (NX, NX, 1), TAU, g0, 2)
+    probe = (time.perf_counter() - t0) / 2
+    full = probe * NSTEPS <= max_s
+    n = NSTEPS - 2 if full else int(max(2, min(200, 12.0 / max(probe, 1e-6))))
     t0 = time.perf_counter()
-    oracle.step(SET, (NX, NX, 1), TAU, g, n)
+    g = oracle.step(SET, (NX, NX, 1), TAU, g, n)
     dt = time.perf_counter() - t0
+    rho_ora = oracle.moments(SET, g)[0] if full else None
     # the same oracle on one thread, a few steps of the same grid (reported beside, not the value)
     oracle.set_threads(1)
     n1 = 4
     t0 = time.perf_counter()
-    oracle.step(SET, (NX, NX, 1), TAU, g, n1)
+    oracle.step(SET, (NX, NX, 1), TAU, g0, n1)
     dt1 = time.perf_counter() - t0
-    return {"value": round(NX * NX * n / dt / 1e6, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{NX}x{NX} D2Q5 FP64, {n} steps, {cores} OpenMP threads, {dt:.1f} s",
+    what = "the whole job (steps 3..1000 timed)" if full else f"{n} steps"
+    line = {"value": round(NX * NX * n / dt / 1e6, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{NX}x{NX} D2Q5 FP64, {what}, {cores} OpenMP threads, {dt:.1f} s",
             "single_thread": {"value": round(NX * NX * n1 / dt1 / 1e6, 2), "unit": "MLUPS",
                               "sample": f"{NX}x{NX} D2Q5 FP64, {n1} steps, 1 thread, {dt1:.1f} s"}}
+    return line, rho_ora
+
+
+def rel_l2_vs_oracle(rho_gpu, rho_ora) -> dict:
+    """Relative L2 error of the timed job's rho' (FP32 storage and arithmetic) against the FP64
+    oracle run of the same job (the space L2 norm of Sec. 9 at the final time)."""
+    if rho_ora is None:
+        return {"value": None, "reason": "oracle job too slow on this host; not compared"}
+    err = float(np.linalg.norm(rho_gpu - rho_ora) / np.linalg.norm(rho_ora))
+    return {"value": err, "field": "rho'", "against": "FP64 oracle, the same 1000-step job", "tolerance": 1e-5}
 
 
 def forms_3d():
@@ -648,13 +681,13 @@ def run_reference(args, rank, world):
         oracle.step(SET, (NX, NX, 1), TAU, g0, sample_steps)
     dt = time.perf_counter() - t0
     value = NX * NX * sample_steps * args.steps / dt / 1e6
-    sample = f"{NX}x{NX} D2Q5 FP64, {sample_steps} steps per timed step, {cores} OpenMP threads"
-    return {"impl": "reference", "metric": "MLUPS (2D D2Q5 FP32 stream-collide job) and fraction of HBM roofline",
+    sample = (f"{NX}x{NX} D2Q5 FP64, {sample_steps} steps per timed step, {cores} OpenMP threads "
+              "(oracle: plain FP64 C restatement of the paper's update, bounded sample)")
+    return {"impl": "reference", "metric": METRIC,
             "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": NX * NX, "velset": SET, "tau": TAU,
-                       "note": "oracle: plain FP64 C restatement of the paper's update, bounded sample"},
+            "config": bench_config(world),
             "cpu_baseline": {"value": round(value, 2), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 2), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -669,6 +702,8 @@ def main(argv=None):
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=sorted(CASES), help="time one configuration alone (profiling)")
+    ap.add_argument("--clocks-out", default=None,
+                    help="keep the nvidia-smi clock samples of the timed region in this CSV ({rank} = rank)")
     args = ap.parse_args(argv)
     if args.case:
         return run_case(args)
@@ -680,10 +715,11 @@ def main(argv=None):
         if line is not None:
             print(json.dumps(line), flush=True)
         return 0
-    line = run_ours(args, rank, world, local)
+    line, rho_gpu = run_ours(args, rank, world, local)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"], rho_ora = cpu_baseline()
+            line["rel_l2_vs_f64"] = rel_l2_vs_oracle(rho_gpu, rho_ora)
         if world == 1 and not args.no_forms:
             line["forms"] = forms_3d()
             line["forms_configs"] = forms_configs()

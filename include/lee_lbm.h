@@ -230,6 +230,14 @@ const char *lee_lbm_last_error(lee_lbm *h);
 /* Frees the handle and its device memory.  NULL-safe.  Synchronises the stream first. */
 lee_status lee_lbm_destroy(lee_lbm *h);
 
+/* Test hook for the failure path (the paper has no counterpart).  after >= 0 arms it: of the CUDA
+ * calls that solver, batch and network handles check from now on, the (after+1)-th that succeeds
+ * is reported as failed (cudaErrorUnknown), once; the handle that made it returns LEE_ERR_CUDA and
+ * is poisoned exactly as after a real CUDA error.  after = -1 disarms it.  No GPU error is raised
+ * (the call itself ran normally), so tests can exercise poisoning from the host.  Process-wide;
+ * LEE_ERR_INVALID_ARGUMENT for after < -1. */
+lee_status lee_test_inject_cuda_error(int32_t after);
+
 /* The global sums of lee_lbm_reduce (same out[D+4] layout and order, same result bit for bit)
  * for a population field the caller owns, computed WITHOUT ALLOCATING anything.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc (or any routine
@@ -237,7 +245,8 @@ lee_status lee_lbm_destroy(lee_lbm *h);
  * budget or allocator, a process that reserves all its device memory up front, or a callback
  * that must not allocate -- and therefore cannot create a solver handle, whose creation
  * allocates the reduction scratch.
- *   set, storage: as in lee_lbm_config; g: DEVICE pointer to the stored populations,
+ *   set: as in lee_lbm_config; storage: LEE_STORE_F64, F32, F16 or BF16 (SPLIT16 and the other
+ *   multi-array forms are rejected with LEE_ERR_INVALID_ARGUMENT); g: DEVICE pointer to the stored populations,
  *   g[i * pitch + cell] for i < q, in the storage type (16-bit storage holds S * g_i / f*_i);
  *   cells: 1 .. 2^31 - 1; pitch >= cells (elements between velocity arrays);
  *   store_scale: S for 16-bit storage (> 0), ignored otherwise;
@@ -246,7 +255,9 @@ lee_status lee_lbm_destroy(lee_lbm *h);
  * every GPU loading the library keeps until the process exits.  Sizes beyond it (more than
  * 2^31 - 1 cells) are rejected with LEE_ERR_INVALID_ARGUMENT; so are bad pointers or enums.
  * Set-up: the first call on a device (with that device current) looks up the array's device
- * address once; make that first call before any stream capture.  All calls share the one array
+ * address once and keeps it; make that first call before any stream capture.  The kept address
+ * belongs to the device's primary context: after cudaDeviceReset on that device it is stale, and
+ * this entry point must not be called again in that process.  All calls share the one array
  * and each call overwrites the entries it reads, so nothing needs clearing between calls -- but
  * calls that overlap on the GPU (e.g. on two streams at once) race on it.  Asynchronous: returns
  * after enqueueing; a CUDA failure returns LEE_ERR_CUDA (there is no handle to poison). */

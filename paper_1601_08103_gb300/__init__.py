@@ -90,6 +90,7 @@ _SIGS = {
     "lee_lbm_last_error": (ctypes.c_char_p, [_P]),
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
     "lee_reduce_noalloc": (ctypes.c_int, [_I32, _I32, _P, _I64, _I64, _D, _P, _P]),
+    "lee_test_inject_cuda_error": (ctypes.c_int, [_I32]),
     # include/lee_batch.h
     "lee_batch_create": (ctypes.c_int, [_I32, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
     "lee_batch_init_fields": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I32]),
@@ -301,18 +302,62 @@ def lee_lbm_destroy(h):
         _check(_lib.lee_lbm_destroy(h), "lee_lbm_destroy")
 
 
+NOALLOC_DTYPES = {"f64": "float64", "f32": "float32", "f16": "float16", "bf16": "bfloat16"}
+
+
+def _noalloc_check(set_name: str, storage: str, g, cells: int, pitch: int, out):
+    """Host-side checks of lee_reduce_noalloc's buffers, which the C side cannot make: the dtype
+    of g matches the storage, g holds (q - 1) * pitch + cells elements, out is FP64 with D + 4
+    entries, and both are CUDA tensors on the current device.  Raises ValueError; launches
+    nothing."""
+    if storage not in NOALLOC_DTYPES:
+        raise ValueError(f"lee_reduce_noalloc: storage {storage!r} is not accepted (f64, f32, f16, bf16)")
+    info = lee_velset_info(set_name)
+    q, D = info["q"], info["D"]
+    for name, t in (("g", g), ("out", out)):
+        if not (hasattr(t, "dtype") and hasattr(t, "numel") and hasattr(t, "is_cuda")):
+            raise ValueError(f"lee_reduce_noalloc: {name} must be a torch tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"lee_reduce_noalloc: {name} must be contiguous")
+    if str(g.dtype).replace("torch.", "") != NOALLOC_DTYPES[storage]:
+        raise ValueError(f"lee_reduce_noalloc: g is {g.dtype}, storage {storage} needs {NOALLOC_DTYPES[storage]}")
+    cells, pitch = int(cells), int(pitch)
+    if cells < 1 or pitch < cells:
+        raise ValueError("lee_reduce_noalloc: need 1 <= cells <= pitch")
+    if g.numel() < (q - 1) * pitch + cells:
+        raise ValueError(f"lee_reduce_noalloc: g holds {g.numel()} elements, the layout needs {(q - 1) * pitch + cells}")
+    if str(out.dtype) != "torch.float64" or out.numel() < D + 4:
+        raise ValueError(f"lee_reduce_noalloc: out must be float64 with at least {D + 4} entries")
+    if not (g.is_cuda and out.is_cuda):
+        raise ValueError("lee_reduce_noalloc takes device buffers only")
+    import torch
+
+    cur = torch.cuda.current_device()
+    if g.device.index != cur or out.device.index != cur:
+        raise ValueError("lee_reduce_noalloc: g and out must be on the current CUDA device")
+
+
 def lee_reduce_noalloc(set_name: str, storage: str, g, cells: int, pitch: int, out, store_scale: float = 1.0,
                        stream=None):
     """Global sums of a caller-owned device population field without any allocation (see
-    include/lee_lbm.h).  g and out must be CUDA tensors; out holds D + 4 doubles."""
+    include/lee_lbm.h).  g and out must be CUDA tensors on the current device; out holds D + 4
+    doubles.  Runs on `stream` (a torch stream or a raw handle), by default torch's current
+    stream, so it is ordered after the kernels that produced g."""
+    _noalloc_check(set_name, storage, g, cells, pitch, out)
     lib = load()
-    ga, gon = _addr(g)
-    oa, oon = _addr(out)
-    if not (gon and oon):
-        raise ValueError("lee_reduce_noalloc takes device buffers only")
-    st = None if stream is None else (stream if isinstance(stream, int) else int(stream.cuda_stream))
-    _check(lib.lee_reduce_noalloc(SETS[set_name], STORAGE[storage], ga, int(cells), int(pitch), float(store_scale), oa,
-                                  st), "lee_reduce_noalloc")
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    st = stream if isinstance(stream, int) else int(stream.cuda_stream)
+    _check(lib.lee_reduce_noalloc(SETS[set_name], STORAGE[storage], g.data_ptr(), int(cells), int(pitch),
+                                  float(store_scale), out.data_ptr(), st), "lee_reduce_noalloc")
+
+
+def lee_test_inject_cuda_error(after: int):
+    """Test hook (include/lee_lbm.h): the (after+1)-th successful CUDA call that a handle checks
+    from now on is reported as failed, once; -1 disarms."""
+    _check(load().lee_test_inject_cuda_error(int(after)), "lee_test_inject_cuda_error")
 
 
 def lee_stability_scan(set_name: str, tau: float, m: int, rho, lam=None, kappa=None, nu=None, delta: float = 1e-6,

@@ -103,7 +103,7 @@ lee_status bfail(lee_batch *b, lee_status s, const std::string &m) {
 
 #define BCK(b, call, what)                                                                       \
     do {                                                                                         \
-        cudaError_t e_ = (call);                                                                 \
+        cudaError_t e_ = lee::checked(call);                                                     \
         if (e_ != cudaSuccess)                                                                   \
             return bfail((b), e_ == cudaErrorMemoryAllocation ? LEE_ERR_OUT_OF_MEMORY : LEE_ERR_CUDA, \
                          std::string(what) + ": " + cudaGetErrorString(e_));                      \
@@ -112,7 +112,7 @@ lee_status bfail(lee_batch *b, lee_status s, const std::string &m) {
 lee_status benter(lee_batch *b) {
     if (!b) return LEE_ERR_INVALID_ARGUMENT;
     if (b->poisoned) return LEE_ERR_POISONED;
-    cudaError_t e = cudaSetDevice(b->device);
+    cudaError_t e = lee::checked(cudaSetDevice(b->device));
     if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, "cudaSetDevice");
     return LEE_OK;
 }

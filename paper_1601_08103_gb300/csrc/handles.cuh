@@ -56,6 +56,11 @@ struct lee_lbm {
 };
 
 namespace lee {
+// Every CUDA status the handles check passes through here.  Normally it returns e unchanged; after
+// lee_test_inject_cuda_error(n) the (n+1)-th successful call checked from then on is reported as
+// cudaErrorUnknown instead (once), so that tests can drive a handle into its failure path from the
+// host without any real GPU error.
+cudaError_t checked(cudaError_t e);
 using BatchedFn = cudaError_t (*)(const void *, void *, const void *, const unsigned short *, int, int, cudaStream_t);
 using BatchedTbFn = cudaError_t (*)(const void *, void *, const void *, const void *, int, cudaStream_t);
 }

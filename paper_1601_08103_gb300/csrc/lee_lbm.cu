@@ -1,6 +1,7 @@
 // lee_lbm.cu -- C ABI of the solver (include/lee_lbm.h): handle, memory, validation, dispatch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -110,6 +111,20 @@ void fold_coefficients(int set, bool scaled, double omega, double M[4][4], doubl
     }
 }
 
+// Host-side failure injection for tests (lee_test_inject_cuda_error): number of successful
+// checked calls still to pass before one is reported as failed; negative = disarmed.
+std::atomic<int> g_inject_countdown{-1};
+
+cudaError_t checked(cudaError_t e) {
+    if (e != cudaSuccess) return e;
+    int n = g_inject_countdown.load(std::memory_order_relaxed);
+    while (n >= 0) {
+        if (g_inject_countdown.compare_exchange_weak(n, n - 1, std::memory_order_relaxed))
+            return n == 0 ? cudaErrorUnknown : cudaSuccess;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace lee
 
 using namespace lee;
@@ -152,14 +167,14 @@ lee_status cuda_fail(lee_lbm *h, cudaError_t e, const char *what) {
 
 #define LEE_CK(h, call, what)                                 \
     do {                                                      \
-        cudaError_t e_ = (call);                              \
+        cudaError_t e_ = lee::checked(call);                  \
         if (e_ != cudaSuccess) return cuda_fail((h), e_, what); \
     } while (0)
 
 lee_status enter(lee_lbm *h) {
     if (!h) return LEE_ERR_INVALID_ARGUMENT;
     if (h->poisoned) return LEE_ERR_POISONED;
-    cudaError_t e = cudaSetDevice(h->device);
+    cudaError_t e = lee::checked(cudaSetDevice(h->device));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     return LEE_OK;
 }
@@ -242,6 +257,12 @@ const char *lee_status_string(lee_status s) {
     case LEE_ERR_POISONED: return "handle poisoned by an earlier CUDA error";
     default: return "unknown status";
     }
+}
+
+lee_status lee_test_inject_cuda_error(int32_t after) {
+    if (after < -1) return LEE_ERR_INVALID_ARGUMENT;
+    g_inject_countdown.store(after, std::memory_order_relaxed);
+    return LEE_OK;
 }
 
 lee_status lee_velset_info(int32_t set, int32_t *D, int32_t *q, int32_t *c, double *f, double *beta, double *consts) {

@@ -582,7 +582,7 @@ namespace {
 
 #define MCK(mm, call)                                                      \
     do {                                                                   \
-        cudaError_t e_ = (call);                                           \
+        cudaError_t e_ = lee::checked(call);                               \
         if (e_ != cudaSuccess) {                                           \
             (mm)->poisoned = true;                                         \
             (mm)->err = cudaGetErrorString(e_);                            \
@@ -593,7 +593,11 @@ namespace {
 lee_status menter(lee_mlp *m) {
     if (!m) return LEE_ERR_INVALID_ARGUMENT;
     if (m->poisoned) return LEE_ERR_POISONED;
-    if (cudaSetDevice(m->device) != cudaSuccess) return LEE_ERR_CUDA;
+    if (lee::checked(cudaSetDevice(m->device)) != cudaSuccess) {
+        m->poisoned = true;
+        m->err = "cudaSetDevice";
+        return LEE_ERR_CUDA;
+    }
     return LEE_OK;
 }
 

@@ -154,10 +154,15 @@ inline ReduceCombine make_reduce_combine(const SetOps *o, const SetConsts &k, bo
     return c;
 }
 
+// Most blocks a grid-stride auxiliary kernel is launched with (16 per SM on 152 SMs).  The
+// reduction writes one row of partials per block, so this is also the row count of every
+// partial-sum buffer, including the fixed scratch of the allocation-free reduction.
+constexpr int kMaxAuxBlocks = 152 * 16;
+
 // Grid size for grid-stride auxiliary kernels.
 inline int aux_blocks(long long cells, int threads = 256) {
     long long b = (cells + threads - 1) / threads;
-    if (b > 152LL * 16) b = 152LL * 16;
+    if (b > kMaxAuxBlocks) b = kMaxAuxBlocks;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -28,7 +28,8 @@ using namespace lee;
 
 namespace {
 
-constexpr int kMaxPartials = 152 * 16;  // = aux_blocks() upper bound
+constexpr int kMaxPartials = kMaxAuxBlocks;  // rows of partials: the most blocks aux_blocks() gives
+static_assert(kMaxPartials * kReduceMax * sizeof(double) == 311296, "scratch size as documented in lee_lbm.h");
 constexpr int kMaxDevices = 64;
 
 // Scratch for the block partials.  In host code this name is only a stand-in for the device

@@ -55,7 +55,18 @@ def test_reference_arm_contract(monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert bench.run_reference(args, 1, 2) is None  # other ranks print nothing
+    assert line["config"] == bench.bench_config(1)  # the same workload description as our arm
     json.dumps(line)
+
+
+def test_headline_error_against_oracle():
+    import numpy as np
+
+    want = np.linspace(1.0, 2.0, 16)
+    got = want * (1 + 1e-7)
+    r = bench.rel_l2_vs_oracle(got, want)
+    assert abs(r["value"] - 1e-7) < 1e-12 and r["field"] == "rho'"
+    assert bench.rel_l2_vs_oracle(got, None)["value"] is None
 
 
 def test_profiled_traffic_is_null_when_kernel_changed(tmp_path, monkeypatch):

@@ -41,9 +41,10 @@ def _errors(lee, name, Ns, tau, a=20.0, storage="f64"):
 
 
 def _record(key, Ns, errs):
-    out = os.path.join(os.path.dirname(os.path.dirname(__file__)), "gpurun_out")
-    if os.path.isdir(out):
-        path = os.path.join(out, "convergence.jsonl")
+    """Appends the measured errors and orders to the JSON-lines file named by LEE_CONVERGENCE_LOG,
+    if that variable is set (nothing is written otherwise)."""
+    path = os.environ.get("LEE_CONVERGENCE_LOG")
+    if path:
         with open(path, "a") as f:
             f.write(json.dumps({"case": key, "N": list(Ns), "err": errs.tolist(),
                                 "order": np.log2(errs[:-1] / errs[1:]).tolist()}) + "\n")

@@ -113,3 +113,37 @@ def test_stability_scan_rejects_bad_arguments_on_the_host(lib):
     fake = 16  # never dereferenced: every call below fails validation first
     for args in [(0, -1.0, 8, 1e-6), (0, 0.5, 0, 1e-6), (0, 0.5, 8, 0.0), (42, 0.5, 8, 1e-6), (6, 0.5, 300, 1e-6)]:
         assert raw.lee_stability_scan(*args, None, fake, None, None, None) == lee.LEE_ERR_INVALID_ARGUMENT, args
+
+
+def test_noalloc_binding_rejects_bad_buffers_without_launching(lib):
+    """lee_reduce_noalloc's binding checks what the C side cannot (dtype against storage, buffer
+    sizes, FP64 output, device placement) and raises before any launch; CPU tensors stand in for
+    the caller's buffers, so these checks run without a GPU."""
+    import torch
+
+    q, D, cells = 5, 2, 64
+    g = torch.zeros((q, cells), dtype=torch.float64)
+    out = torch.zeros(D + 4, dtype=torch.float64)
+    bad = [
+        dict(g=g.float()),                                       # dtype does not match f64 storage
+        dict(storage="split16"),                                 # multi-array storage not accepted
+        dict(g=torch.zeros((q - 1, cells), dtype=torch.float64)),  # too few elements for q arrays
+        dict(pitch=cells + 8),                                   # layout with pitch needs more elements
+        dict(cells=0),
+        dict(out=torch.zeros(D + 4, dtype=torch.float32)),        # out must be FP64
+        dict(out=torch.zeros(D + 3, dtype=torch.float64)),        # out too short
+        dict(g=torch.zeros((q, 2 * cells), dtype=torch.float64)[:, ::2]),  # not contiguous
+        dict(g=np.zeros((q, cells))),                            # not a tensor
+        dict(),                                                  # host tensors: device buffers only
+    ]
+    for kw in bad:
+        args = dict(set_name="D2Q5", storage="f64", g=g, cells=cells, pitch=cells, out=out)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            lee.lee_reduce_noalloc(args["set_name"], args["storage"], args["g"], args["cells"], args["pitch"],
+                                   args["out"])
+
+
+def test_injection_hook_validates_its_argument(lib):
+    assert lib.lee_test_inject_cuda_error(-2) == lee.LEE_ERR_INVALID_ARGUMENT
+    assert lib.lee_test_inject_cuda_error(-1) == lee.LEE_OK

@@ -27,8 +27,11 @@ def reference_sums(name, storage, g64_dev, scale):
     return out
 
 
-@pytest.mark.parametrize("name,storage", [("D2Q5", "f64"), ("D3Q19", "f32"), ("D3Q7", "f16")])
+@pytest.mark.parametrize("name,storage", [("D2Q5", "f64"), ("D3Q19", "f32"), ("D3Q7", "f16"), ("D2Q5_DI", "bf16"),
+                                          ("D1Q3", "f32"), ("D1Q3", "bf16")])
 def test_noalloc_matches_handle_reduce_on_two_calls_in_a_row(gpu_lib, name, storage):
+    """Bit for bit against lee_lbm_reduce on a handle holding the same stored values, on two calls
+    in a row with different data (the second call reuses the shared scratch the first one left)."""
     import torch
 
     info = lee.lee_velset_info(name)
@@ -36,22 +39,20 @@ def test_noalloc_matches_handle_reduce_on_two_calls_in_a_row(gpu_lib, name, stor
     cells = 96 * 1024 + 16  # several block tiles and a ragged tail; divisible by 16 for the shapes
     f = torch.tensor(info["f"], dtype=torch.float64, device="cuda")[:, None]
     scale = 1024.0 if storage in ("f16", "bf16") else 1.0
+    dtype = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[storage]
     for call, seed in enumerate((5, 6)):  # two calls in a row, different data
-        g64 = torch.from_numpy(inputs.random_populations(q, cells, seed)).cuda()
-        want = reference_sums(name, storage, g64, scale if storage == "f16" else 0.0)
-        # the caller's stored populations, in the storage format the library documents
-        if storage == "f64":
-            stored = g64.clone()
-        elif storage == "f32":
-            stored = g64.float()
-        else:
-            stored = (g64 * (scale / f)).half()
+        # the caller's stored populations, in the storage format the library documents (16-bit:
+        # S g / f*); the handle gets their exact FP64 values, which it stores back bit for bit
+        raw = torch.from_numpy(inputs.random_populations(q, cells, seed, scale=1.0)).cuda()
+        stored = raw.to(dtype)
+        g64 = stored.double() * (f / scale) if storage in ("f16", "bf16") else stored.double()
+        want = reference_sums(name, storage, g64, scale if storage in ("f16", "bf16") else 0.0)
         pitch = cells
         out = torch.full((D + 4,), float("nan"), dtype=torch.float64, device="cuda")
         lee.lee_reduce_noalloc(name, storage, stored, cells, pitch, out, store_scale=scale)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300, err_msg=f"call {call}")
+        assert np.array_equal(got, want), (call, got, want)
 
 
 def test_noalloc_rejects_bad_arguments(gpu_lib):
