@@ -380,7 +380,7 @@ def forms_3d():
     out = {}
     ref = None
     stream = torch.cuda.current_stream()
-    for storage in ("f64", "f32", "f16", "bf16"):
+    for storage in ("f64", "f32", "f16", "bf16", "bfp16"):
         with lee.Solver("D3Q7", (n, n, n), 0.55, storage=storage, stream=stream) as sv:
             sv.init_fields(rho_d, u_d, th_d)
             sv.step(2)
@@ -396,11 +396,86 @@ def forms_3d():
             ms = e0.elapsed_time(e1)
         if storage == "f64":
             ref = r
+            spl = sv.steps_per_launch
         err = float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))
         bpl = 2 * 7 * lee.STORAGE_BYTES[storage]
         out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
-                        "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "rel_l2_rho_vs_f64": err}
-    return {"workload": "3D D3Q7 periodic 384^3, tau=0.55, pulse A=1e-3 w=16, 500 steps", "storage": out}
+                        "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "rel_l2_rho_vs_f64": err,
+                        "steps_per_launch": spl, "bytes_per_update": round(bpl / max(spl, 1), 3)}
+    for storage in ("f16", "bf16", "bfp16"):
+        out[storage]["mlups_gain_vs_f32"] = round(out[storage]["mlups"] / out["f32"]["mlups"], 3)
+    return {"workload": "3D D3Q7 periodic 384^3, tau=0.55, pulse A=1e-3 w=16, 500 steps", "storage": out,
+            "error_reference": "the FP64 run on the GPU, which the tests hold to the oracle within 1e-12 "
+                               "(test_full_size_3d_config_against_oracle also checks every storage against "
+                               "the oracle directly)"}
+
+
+def _device_config_2d(n: int, seed: int = 2):
+    """The 2D configuration's field (Gaussian pulse A = 1e-3, w = 32, plus 8 density plane waves of
+    amplitude 1e-4, wavelength 16-256 cells) on an n x n grid, drawn from the same random sequence
+    as inputs.config_2d but evaluated on the device (8192^2 would need gigabytes on the host)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0, n, size=2)
+    rho = _device_pulse((n, n, 1), 1e-3, 32.0, [c[0], c[1], 0.0])
+    lo, hi = max(1.0, n / 256.0), max(1.0, n / 16.0)
+    ax = torch.arange(n, dtype=torch.float64, device="cuda")
+    for _ in range(8):
+        while True:
+            kmag = rng.uniform(lo, hi)
+            ang = rng.uniform(0, 2 * np.pi)
+            m = (int(round(kmag * np.cos(ang))), int(round(kmag * np.sin(ang))))
+            if m[0] != 0 or m[1] != 0:
+                break
+        ph = rng.uniform(0, 2 * np.pi)
+        arg = (2 * np.pi * m[0] / n) * ax[None, :] + (2 * np.pi * m[1] / n) * ax[:, None] + ph
+        rho += 1e-4 * torch.cos(arg).reshape(-1)
+    return rho
+
+
+def forms_mixed_2d(n: int = 8192, steps: int = 1000):
+    """The mixed-precision storage forms on a 2D grid far beyond L2 (D2Q5, n^2, tau = 0.6, the 2D
+    configuration's pulse and plane waves, 1000 steps): MLUPS, bytes per update of the kernel that
+    ran, and the relative L2 error of rho' against the FP64 run."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+
+    cells = n * n
+    stream = torch.cuda.current_stream()
+    rho = _device_config_2d(n)
+    u = torch.zeros((2, cells), dtype=torch.float64, device="cuda")
+    th = torch.zeros(cells, dtype=torch.float64, device="cuda")
+    out, ref = {}, None
+    for storage in ("f64", "f32", "f16", "bfp16"):
+        with lee.Solver("D2Q5", (n, n, 1), 0.6, storage=storage, stream=stream) as sv:
+            sv.init_fields(rho, u, th)
+            sv.step(8)
+            sv.init_fields(rho, u, th)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sv.step(steps)
+            e1.record(stream)
+            r = torch.empty(cells, dtype=torch.float64, device="cuda")
+            sv.moments(r, None, None)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            spl = sv.steps_per_launch
+        if ref is None:
+            ref = r
+        bpl = 2 * 5 * lee.STORAGE_BYTES[storage]
+        out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1), "steps_per_launch": spl,
+                        "bytes_per_update": round(bpl / spl, 3),
+                        "gbs_algorithmic_per_launch": round(bpl * cells * steps / spl / (ms / 1e3) / 1e9, 1),
+                        "rel_l2_rho_vs_f64": float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))}
+        del r
+        torch.cuda.empty_cache()
+    for storage in ("f16", "bfp16"):
+        out[storage]["mlups_gain_vs_f32"] = round(out[storage]["mlups"] / out["f32"]["mlups"], 3)
+    return {"workload": f"2D D2Q5 periodic {n}x{n}, tau=0.6, pulse+8 plane waves, {steps} steps", "storage": out,
+            "error_reference": "the FP64 run on the GPU (held to the oracle by the tests)"}
 
 
 def _device_pulse(shape, amplitude: float, width: float, center):
@@ -549,6 +624,7 @@ def forms_batched(steps: int = 1000):
     stream = torch.cuda.current_stream()
     out = {}
     rho_by = {}
+    out_shape = None
     for storage, mode in (("f64", "graph"), ("f32", "sequential"), ("f32", "launch"), ("f32", "graph")):
         with lee.Batch("D2Q5", storage, doms, stream=stream) as b:
             cells = b.cells
@@ -571,19 +647,47 @@ def forms_batched(steps: int = 1000):
                 off += nx * ny
             torch.cuda.synchronize()
             shape = b.tune() if mode != "sequential" else None
-        rho_by[(storage, mode)] = rho
+            if mode == "graph" and storage == "f32":
+                out_shape = b.tune_shape()
         key = f"{storage}_{mode}"
         out[key] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1), "ms": round(ms, 3),
                     "gbs": round(2 * 5 * lee.STORAGE_BYTES[storage] * cells * steps / (ms / 1e3) / 1e9, 1)}
         if shape:
             out[key]["tuned_threads_cells_per_thread"] = list(shape)
+        rho_by[(storage, mode)] = rho
+    # the fair baseline: every domain through its own best single-domain path (lee_lbm_step, four
+    # fused steps per launch replayed from a CUDA graph), one domain after the other
+    solvers = [lee.Solver("D2Q5", (nx, ny, 1), tau, storage="f32", stream=stream) for nx, ny, tau in doms]
+    for sv, f in zip(solvers, fields):
+        sv.init_fields(*f)
+        sv.step(steps)  # warm-up: graph capture
+        sv.init_fields(*f)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for sv in solvers:
+        sv.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pd = e0.elapsed_time(e1)
+    rho_pd = torch.cat([torch.empty(nx * ny, dtype=torch.float64, device="cuda") for nx, ny, _ in doms])
+    off = 0
+    for sv, (nx, ny, _) in zip(solvers, doms):
+        sv.moments(rho_pd[off: off + nx * ny], None, None)
+        off += nx * ny
+        sv.close()
+    torch.cuda.synchronize()
+    out["f32_per_domain_best"] = {"mlups": round(cells * steps / (ms_pd / 1e3) / 1e6, 1), "ms": round(ms_pd, 3),
+                                  "bit_equal_to_batched": bool(torch.equal(rho_pd, rho_by[("f32", "graph")]))}
     ref = rho_by[("f64", "graph")]
     for (storage, mode), r in rho_by.items():
         out[f"{storage}_{mode}"]["rel_l2_rho_vs_f64"] = float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))
     seq = out["f32_sequential"]["ms"]
     return {"workload": f"96 periodic D2Q5 domains, {cells} cells, FP32, {steps} steps", "modes": out,
+            "tuned_shape": out_shape,
             "speedup_graph_vs_sequential": round(seq / out["f32_graph"]["ms"], 3),
-            "speedup_launch_vs_sequential": round(seq / out["f32_launch"]["ms"], 3)}
+            "speedup_launch_vs_sequential": round(seq / out["f32_launch"]["ms"], 3),
+            "speedup_graph_vs_per_domain_best": round(ms_pd / out["f32_graph"]["ms"], 3)}
 
 
 def forms_learned(n: int = 1024, steps: int = 3000):
@@ -616,6 +720,11 @@ CASES = {
     "d2q5_f32_4096": ("D2Q5", (4096, 4096, 1), "f32", 0.6),
     "d2q5_f32_8192": ("D2Q5", (8192, 8192, 1), "f32", 0.6),
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
+    "d2q5_bfp16_8192": ("D2Q5", (8192, 8192, 1), "bfp16", 0.6),
+    "d2q5_bfp16": ("D2Q5", (2048, 2048, 1), "bfp16", 0.6),
+    "d3q7_bfp16": ("D3Q7", (384, 384, 384), "bfp16", 0.55),
+    "d3q7_bfp16_256": ("D3Q7", (256, 256, 256), "bfp16", 0.55),
+    "d3q19_bfp16": ("D3Q19", (256, 256, 256), "bfp16", 0.55),
     "d3q7_f32_odd": ("D3Q7", (385, 383, 381), "f32", 0.55),
     "d2q5_learned_1024": ("D2Q5", (1024, 1024, 1), "f32", 0.6, "open_learned"),
     "d2q5_zero_1024": ("D2Q5", (1024, 1024, 1), "f32", 0.6, "open_zero"),
@@ -722,6 +831,7 @@ def main(argv=None):
             line["rel_l2_vs_f64"] = rel_l2_vs_oracle(rho_gpu, rho_ora)
         if world == 1 and not args.no_forms:
             line["forms"] = forms_3d()
+            line["forms_mixed_2d"] = forms_mixed_2d()
             line["forms_configs"] = forms_configs()
             line["forms_stability"] = forms_stability()
             line["forms_split"] = forms_split()

@@ -48,10 +48,10 @@ lee_status lee_batch_init_fields(lee_batch *b, int32_t d, const double *rho, con
  * LAUNCH call runs the autotuner unless lee_batch_set_tuning fixed the launch shape.  In GRAPH
  * mode a run of up to 4096 steps is one launch of a graph holding all its steps (captured on
  * first use of that length and parity, then cached); longer runs replay a 100-step graph.  With
- * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance four steps per
- * launch (the intermediate states kept in shared memory; tiles of 128 columns x up to 64 rows,
- * dispatched largest first; LEE_TB_STEPS=1..4 in the environment at create time picks another
- * count), bit-identical to single steps. */
+ * FP32 storage and every nx a multiple of 4, GRAPH and LAUNCH modes advance several steps per
+ * launch (the intermediate states kept in shared memory; tiles of 128 columns), with the count,
+ * tile rows and tile order the autotuner picks (lee_batch_tune_shape; LEE_TB_STEPS=1..4 in the
+ * environment at create time fixes the count), bit-identical to single steps. */
 lee_status lee_batch_step(lee_batch *b, int64_t n, int32_t mode);
 
 /* Per-cell moments of domain d (as lee_lbm_moments).  NULL outputs are skipped. */
@@ -63,13 +63,36 @@ lee_status lee_batch_reduce(lee_batch *b, int32_t d, double *out, int32_t on_dev
 /* Post-collision populations of domain d as FP64 g[5][cells_d] (library velocity order). */
 lee_status lee_batch_get_populations(lee_batch *b, int32_t d, double *g, int32_t on_device);
 
-/* Autotuner: times every candidate launch shape (threads per block in {128, 256, 512} x cells
- * per thread in {V/2, V}, V = 16 bytes / storage size) for a few steps on the batch itself and
- * keeps the fastest.  Tuning writes only the idle buffer, so the state does not change.  Results
- * are cached per (set, storage, domain list) for the process, and in the text file named by the
- * environment variable LEE_AUTOTUNE_CACHE when it is set.  *threads and *cells_per_thread
- * receive the choice (either may be NULL). */
+/* Launch shape of a batch: the one-step batched kernel (threads per block, cells per thread) and
+ * the fused multi-step kernel (steps per launch; tiles of 128 columns x tile_rows rows; dispatch
+ * order 0 = tiles with the most rows first, 1 = domain by domain).  steps_per_launch = 1 means
+ * every step runs the one-step kernel.  us_per_step: the tuner's measurement of one time step of
+ * the whole batch with this shape (0 when the shape was set by hand). */
+typedef struct {
+    int32_t threads, cells_per_thread;
+    int32_t steps_per_launch, tile_rows, tile_order;
+    float us_per_step;
+} lee_batch_shape;
+
+/* Autotuner: times every candidate shape for a few launches on the batch itself (CUDA events on
+ * its stream) and keeps the one with the least time per step:
+ *   one-step kernel: threads per block {128, 256, 512} x cells per thread {V/2, V}
+ *     (V = 16 bytes / storage size);
+ *   fused kernel (FP32 storage, every nx a multiple of 4): steps per launch {2, 3, 4} (only the
+ *     count LEE_TB_STEPS fixed at create time, if set) x tile rows {32, 48, 64, 96, 128} x both
+ *     tile orders; it is kept only if it beats the one-step kernel per step.
+ * Every shape gives the same bits.  Tuning writes only the idle buffer, so the state does not
+ * change.  Results are cached per (set, storage, domain list) for the process, and in the text
+ * file named by the environment variable LEE_AUTOTUNE_CACHE when it is set.  lee_batch_tune
+ * reports the one-step part (either pointer may be NULL), lee_batch_tune_shape all of it. */
 lee_status lee_batch_tune(lee_batch *b, int32_t *threads, int32_t *cells_per_thread);
+lee_status lee_batch_tune_shape(lee_batch *b, lee_batch_shape *out);
+
+/* Fixes the whole launch shape instead of tuning: threads and cells_per_thread as for
+ * lee_batch_set_tuning; steps_per_launch 1, or 2..4 where the fused kernel applies, with
+ * tile_rows a multiple of 4 in 4..1024 and tile_order 0 or 1.  LEE_ERR_INVALID_ARGUMENT
+ * otherwise. */
+lee_status lee_batch_set_shape(lee_batch *b, const lee_batch_shape *shape);
 
 /* Fixes the launch shape instead of tuning (threads in {128, 256, 512}; cells_per_thread must
  * divide every nx_d and be one of the tuner's candidates). */

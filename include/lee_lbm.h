@@ -77,8 +77,19 @@ typedef enum {
  *                 of the cell in the frame (1 .. sponge_width, maximum over axes).
  *   OPEN_LEARNED: 2D five-velocity sets only; the entering population of each edge cell is
  *                 predicted by a small MLP from the 3-cell strip along the inward normal
- *                 (lee_lbm_set_boundary_mlp). */
-typedef enum { LEE_BC_PERIODIC = 0, LEE_BC_OPEN_ZERO = 1, LEE_BC_OPEN_SPONGE = 2, LEE_BC_OPEN_LEARNED = 3 } lee_bc;
+ *                 (lee_lbm_set_boundary_mlp).
+ *   SLAB:         the grid is one slab of a larger periodic domain (Sec. 2.2) cut along its last
+ *                 axis (y in 2D, z in 3D; ny resp. nz = the slab's own planes): periodic along the
+ *                 other axes, and along the cut the populations that enter come from the
+ *                 neighbouring slabs through halo planes (lee_lbm_slab_* below).  2D and 3D sets;
+ *                 F64, F32, F16 and BF16 storage. */
+typedef enum {
+    LEE_BC_PERIODIC = 0,
+    LEE_BC_OPEN_ZERO = 1,
+    LEE_BC_OPEN_SPONGE = 2,
+    LEE_BC_OPEN_LEARNED = 3,
+    LEE_BC_SLAB = 4
+} lee_bc;
 
 /* Storage of the populations in device memory.  Collision arithmetic is FP64 for F64 storage and
  * FP32 otherwise.  The 16-bit forms store S * g_i / f*_i rounded to nearest-even, with S a power
@@ -87,13 +98,24 @@ typedef enum { LEE_BC_PERIODIC = 0, LEE_BC_OPEN_ZERO = 1, LEE_BC_OPEN_SPONGE = 2
  * SPLIT16 (periodic grids only) keeps per cell the conserved moments (rho', j, E) in FP32 and the
  * post-collision non-equilibrium parts n*_i = (1 - 1/tau) (g_i - g_i^eq) in FP16 as S n*_i / f*_i:
  * 4 (D + 2) + 2 q bytes per cell and copy (58 B for D3Q19 against 76 B in FP32), with only the
- * small non-equilibrium part rounded to 16 bits.  It pays for the q-heavy sets (D3Q19, D3Q13). */
+ * small non-equilibrium part rounded to 16 bits.  It pays for the q-heavy sets (D3Q19, D3Q13).
+ * BFP16 (block floating point; periodic, zero-incoming and sponge edges) stores g itself with
+ * 16-bit integer mantissas and one exponent byte per block of 8 consecutive cells of a velocity
+ * array: value = (u - 32768) 2^(e - 127), u uint16, e uint8 (0: zero block; 255: the block held a
+ * NaN/Inf and decodes to NaN).  A block of FP32 values v is encoded with e = b - 14, b the biased
+ * exponent of M = max|v|, plus 1 when M's 23 mantissa bits are >= 8387840 (e = 0 if below 1), and
+ * u = rint(v 2^(127 - e)) + 32768 (nearest-even): an error of at most 2^-15 M (1 + 2^-14) per
+ * value; decoded values encode back to themselves.  Layout [q * pitch] uint16 mantissas, then [q * pitch / 8] uint8
+ * exponents (2.125 bytes per value).  Widths that are a multiple of 8 use the multi-step kernels
+ * with the intermediate states in FP32, so the state is rounded once per launch (see
+ * lee_lbm_step). */
 typedef enum {
     LEE_STORE_F64 = 0,
     LEE_STORE_F32 = 1,
     LEE_STORE_F16 = 2,
     LEE_STORE_BF16 = 3,
-    LEE_STORE_SPLIT16 = 4
+    LEE_STORE_SPLIT16 = 4,
+    LEE_STORE_BFP16 = 5
 } lee_storage;
 
 typedef struct {
@@ -168,7 +190,12 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  *    run of n steps is n / 4 such launches and n % 4 single steps;
  *  - periodic 3D FP32 grids of D3Q7 and diatomic D3Q7 with nx a multiple of 4 advance two steps
  *    per launch (a z-marching tile; LEE_TB_STEPS=1 keeps one step per launch);
- *  - a 1D grid whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
+ *  - BFP16 storage on those periodic 2D (four steps, or three with LEE_TB_STEPS=3) and 3D (two
+ *    steps) grids with nx a multiple of 8 uses the same kernels, but keeps the intermediate states
+ *    in FP32 and encodes only the last one: a launch of k steps equals decoding the state, k FP32
+ *    steps and one encoding, bit for bit (LEE_TB_STEPS=1 or 2 keeps one step per launch, which
+ *    equals decode, one FP32 step, encode);
+ *  - a 1D grid (not BFP16) whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
  *  - OPEN_LEARNED: the boundary network runs on a second stream while the step runs with
@@ -207,18 +234,49 @@ lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_devic
  * and then streams with its predictions as the entering populations. */
 lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t nparams);
 
+/* Slab decomposition of a periodic domain along its last axis (a domain larger than one GPU, or
+ * one spread over several processes).  The Sec. 6 update pulls g_i(t+1, x) from x - c_i: in a slab
+ * handle (LEE_BC_SLAB) the pulls of the first and last owned planes along the cut reach one plane
+ * beyond the slab, into halo planes the handle keeps there.  Before each step those halo planes
+ * must hold the neighbouring slabs' post-collision populations that cross the cut (velocities
+ * with c_last = +1 from the slab below, c_last = -1 from the slab above): one exchange of
+ * `crossing` planes per face and step (D2Q5 1, D3Q7 1, D3Q19 5).  lee_lbm_step takes n <= 1 on
+ * a slab handle, since every step needs a fresh exchange.
+ *
+ * Halo messages are device buffers the handle owns, `bytes` each: send_lo (from the first owned
+ * plane, the populations leaving downward), send_hi (from the last owned plane, leaving upward),
+ * recv_lo (what enters from below: the lower neighbour's send_hi) and recv_hi (the upper
+ * neighbour's send_lo); each holds one plane per crossing velocity, in the library's velocity
+ * order, in the storage type.  One exchange: lee_lbm_slab_pack on every slab, then any transport
+ * that moves send_lo to the lower neighbour's recv_hi and send_hi to the upper neighbour's recv_lo
+ * (NCCL, MPI, a P2P copy into the receiver's own buffer, ...), then lee_lbm_slab_unpack, then
+ * lee_lbm_step(h, 1).  pack and unpack are asynchronous on the handle's stream. */
+lee_status lee_lbm_slab_info(lee_lbm *h, int32_t *crossing, int64_t *plane_cells, int64_t *bytes);
+lee_status lee_lbm_slab_buffers(lee_lbm *h, void **send_lo, void **send_hi, void **recv_lo, void **recv_hi);
+lee_status lee_lbm_slab_pack(lee_lbm *h);
+lee_status lee_lbm_slab_unpack(lee_lbm *h);
+
+/* n steps of `count` slabs of one periodic domain held in this process on one device and one
+ * stream, listed in order along the cut (slab k + 1 above slab k; the last one lies below the
+ * first).  Each step: pack every slab, copy every message into its receiver's recv buffer
+ * (cudaMemcpyAsync, device to device, on the shared stream), unpack, one step of every slab.  The
+ * slabs must share set, storage, tau, the extents across the cut, device and stream, else
+ * LEE_ERR_INVALID_ARGUMENT.  Bit for bit the single-domain result of the same storage. */
+lee_status lee_lbm_slab_step(lee_lbm *const *slabs, int32_t count, int64_t n);
+
 /* Number of time steps taken since the last init/set_populations. */
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
 
 /* How lee_lbm_step runs this grid: *steps = 1 (one fused stream-collide launch per time step),
  * 2..4 (periodic 2D FP32 grids with nx a multiple of 4: that many time steps per launch, the
  * intermediate states kept in shared memory -- temporal blocking; 4 unless LEE_TB_STEPS was set
- * at create time; periodic 3D FP32 D3Q7 and diatomic D3Q7 grids with nx a multiple of 4: 2) or
- * 0 (small 1D grid: all steps of a call in one on-chip launch).  All forms give bit-identical
- * results. */
+ * at create time; periodic 3D FP32 D3Q7 and diatomic D3Q7 grids with nx a multiple of 4: 2;
+ * BFP16 storage: 3 or 4 in 2D and 2 in 3D on such grids with nx a multiple of 8) or 0 (small 1D
+ * grid: all steps of a call in one on-chip launch).  All forms give bit-identical results, except
+ * that BFP16 rounds its state once per launch (see lee_lbm_step). */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);
 
-/* The 16-bit storage scale S in use (1 for F64/F32 storage). */
+/* The 16-bit storage scale S in use (1 for F64/F32/BFP16 storage). */
 lee_status lee_lbm_store_scale(lee_lbm *h, double *scale);
 
 /* Blocks until all work on the handle's stream has finished. */

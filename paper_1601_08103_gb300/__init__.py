@@ -17,12 +17,13 @@ LIB_PATH = _build.LIB
 
 # enums of include/lee_lbm.h
 SETS = {"D1Q3": 0, "D2Q5": 1, "D2Q5_DI": 2, "D3Q7": 3, "D3Q9": 4, "D3Q13": 5, "D3Q19": 6, "D3Q7_DI": 7}
-STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "split16": 4}
-BC = {"periodic": 0, "open_zero": 1, "open_sponge": 2, "open_learned": 3}
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "split16": 4, "bfp16": 5}
+BC = {"periodic": 0, "open_zero": 1, "open_sponge": 2, "open_learned": 3, "slab": 4}
+# bytes per stored population (bfp16: a 16-bit mantissa plus an eighth of a block exponent byte)
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "bfp16": 2.125}
 
 
-def state_bytes_per_cell(D: int, q: int, storage: str) -> int:
+def state_bytes_per_cell(D: int, q: int, storage: str) -> float:
     """Bytes of one cell in one state copy: q populations, or for split16 the D + 2 FP32 moments
     and q FP16 non-equilibrium parts."""
     if storage == "split16":
@@ -84,6 +85,12 @@ _SIGS = {
     "lee_lbm_set_populations": (ctypes.c_int, [_P, _P, _I32]),
     "lee_lbm_set_boundary_mlp": (ctypes.c_int, [_P, _P, _I64]),
     "lee_lbm_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "lee_lbm_slab_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "lee_lbm_slab_buffers": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                            ctypes.POINTER(_P)]),
+    "lee_lbm_slab_pack": (ctypes.c_int, [_P]),
+    "lee_lbm_slab_unpack": (ctypes.c_int, [_P]),
+    "lee_lbm_slab_step": (ctypes.c_int, [_P, _I32, _I64]),
     "lee_lbm_store_scale": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
     "lee_lbm_steps_per_launch": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "lee_lbm_sync": (ctypes.c_int, [_P]),
@@ -100,6 +107,8 @@ _SIGS = {
     "lee_batch_get_populations": (ctypes.c_int, [_P, _I32, _P, _I32]),
     "lee_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "lee_batch_set_tuning": (ctypes.c_int, [_P, _I32, _I32]),
+    "lee_batch_tune_shape": (ctypes.c_int, [_P, _P]),
+    "lee_batch_set_shape": (ctypes.c_int, [_P, _P]),
     "lee_batch_cells": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "lee_batch_sync": (ctypes.c_int, [_P]),
     "lee_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -271,6 +280,36 @@ def lee_lbm_set_boundary_mlp(h, params):
     _check(_lib.lee_lbm_set_boundary_mlp(h, a, int(n)), "lee_lbm_set_boundary_mlp", h)
 
 
+def lee_lbm_slab_info(h):
+    """(crossing velocities per face, cells per plane, bytes per halo message) of a slab handle."""
+    c, p, b = _I32(), _I64(), _I64()
+    _check(_lib.lee_lbm_slab_info(h, ctypes.byref(c), ctypes.byref(p), ctypes.byref(b)), "lee_lbm_slab_info", h)
+    return c.value, p.value, b.value
+
+
+def lee_lbm_slab_buffers(h):
+    """Device addresses (send_lo, send_hi, recv_lo, recv_hi) of a slab handle's halo messages."""
+    v = [_P() for _ in range(4)]
+    _check(_lib.lee_lbm_slab_buffers(h, *[ctypes.byref(x) for x in v]), "lee_lbm_slab_buffers", h)
+    return tuple(x.value for x in v)
+
+
+def lee_lbm_slab_pack(h):
+    _check(_lib.lee_lbm_slab_pack(h), "lee_lbm_slab_pack", h)
+
+
+def lee_lbm_slab_unpack(h):
+    _check(_lib.lee_lbm_slab_unpack(h), "lee_lbm_slab_unpack", h)
+
+
+def lee_lbm_slab_step(solvers, n: int):
+    """n steps of the slabs (Solver objects or raw handles, in order along the cut) of one
+    periodic domain held in this process (see include/lee_lbm.h)."""
+    hs = [x.h if hasattr(x, "h") else x for x in solvers]
+    arr = (_P * len(hs))(*hs)
+    _check(load().lee_lbm_slab_step(ctypes.cast(arr, _P), len(hs), int(n)), "lee_lbm_slab_step", hs[0])
+
+
 def lee_lbm_steps_done(h) -> int:
     v = _I64()
     _check(_lib.lee_lbm_steps_done(h, ctypes.byref(v)), "lee_lbm_steps_done")
@@ -414,6 +453,18 @@ class Solver:
     def set_boundary_mlp(self, params):
         lee_lbm_set_boundary_mlp(self.h, params)
 
+    def slab_info(self):
+        return lee_lbm_slab_info(self.h)
+
+    def slab_buffers(self):
+        return lee_lbm_slab_buffers(self.h)
+
+    def slab_pack(self):
+        lee_lbm_slab_pack(self.h)
+
+    def slab_unpack(self):
+        lee_lbm_slab_unpack(self.h)
+
     @property
     def steps_done(self) -> int:
         return lee_lbm_steps_done(self.h)
@@ -455,6 +506,12 @@ BATCH_MODE = {"graph": 0, "launch": 1, "sequential": 2}
 
 class lee_batch_domain(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("tau", ctypes.c_double)]
+
+
+class lee_batch_shape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("cells_per_thread", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("tile_order", ctypes.c_int32), ("us_per_step", ctypes.c_float)]
 
 
 def lee_batch_create(set_name: str, storage: str, domains, stream=None) -> int:
@@ -504,6 +561,20 @@ def lee_batch_set_tuning(b, threads: int, cells_per_thread: int):
     _check(_lib.lee_batch_set_tuning(b, int(threads), int(cells_per_thread)), "lee_batch_set_tuning", batch=b)
 
 
+def lee_batch_tune_shape(b) -> dict:
+    """The launch shape in use after tuning (see include/lee_batch.h), as a dict."""
+    sh = lee_batch_shape()
+    _check(_lib.lee_batch_tune_shape(b, ctypes.byref(sh)), "lee_batch_tune_shape", batch=b)
+    return {name: getattr(sh, name) for name, _ in lee_batch_shape._fields_}
+
+
+def lee_batch_set_shape(b, threads: int, cells_per_thread: int, steps_per_launch: int, tile_rows: int = 64,
+                        tile_order: int = 0):
+    sh = lee_batch_shape(int(threads), int(cells_per_thread), int(steps_per_launch), int(tile_rows),
+                         int(tile_order), 0.0)
+    _check(_lib.lee_batch_set_shape(b, ctypes.byref(sh)), "lee_batch_set_shape", batch=b)
+
+
 def lee_batch_cells(b) -> int:
     v = _I64()
     _check(_lib.lee_batch_cells(b, ctypes.byref(v)), "lee_batch_cells")
@@ -548,6 +619,12 @@ class Batch:
 
     def set_tuning(self, threads, cells_per_thread):
         lee_batch_set_tuning(self.b, threads, cells_per_thread)
+
+    def tune_shape(self) -> dict:
+        return lee_batch_tune_shape(self.b)
+
+    def set_shape(self, threads, cells_per_thread, steps_per_launch, tile_rows=64, tile_order=0):
+        lee_batch_set_shape(self.b, threads, cells_per_thread, steps_per_launch, tile_rows, tile_order)
 
     @property
     def cells(self) -> int:

@@ -3,7 +3,7 @@
 // They run once per job, not per time step.
 #pragma once
 
-#include "kernels.cuh"
+#include "bfp.cuh"
 
 namespace lee {
 
@@ -205,7 +205,7 @@ __device__ __forceinline__ bool shell_sums(const T *__restrict__ g, long long pi
     static_for<S::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int k = shell_slot<S>(S::shell(i));
-        const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+        const double v = (double)load_elem<S, T>(g, pitch, (long long)i * pitch + x);
         finite = finite && isfinite(v);
         P[k] += v;
         Sq[k] = fma(v, v, Sq[k]);
@@ -274,13 +274,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_partial(const T *__re
             // count the non-finite values of this cell; its finite ones still add up
             static_for<S::Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+                const double v = (double)load_elem<S, T>(g, pitch, (long long)i * pitch + x);
                 if (!isfinite(v)) acc[NR - 1] += 1.0;
             });
             static_for<S::Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int k = shell_slot<S>(S::shell(i));
-                const double v = (double)Store<T>::load(g[(long long)i * pitch + x]);
+                const double v = (double)load_elem<S, T>(g, pitch, (long long)i * pitch + x);
                 if (isfinite(v)) {
                     acc[k] += v;
                     acc[NS + k] = fma(v, v, acc[NS + k]);
@@ -338,7 +338,7 @@ __global__ void k_export(const T *__restrict__ g, long long cells, long long pit
     for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cells; x += (long long)gridDim.x * blockDim.x) {
         static_for<S::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            out[(long long)i * cells + x] = decode<S>((double)Store<T>::load(g[(long long)i * pitch + x]), i, k, scaled);
+            out[(long long)i * cells + x] = decode<S>((double)load_elem<S, T>(g, pitch, (long long)i * pitch + x), i, k, scaled);
         });
     }
 }
@@ -355,6 +355,133 @@ __global__ void k_import(const double *__restrict__ in, long long cells, long lo
             g[(long long)i * pitch + x] = Store<T>::make((typename Store<T>::C)st);
         });
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// slab halos: a grid that is one slab of a periodic domain cut along its last axis
+// ---------------------------------------------------------------------------------------------
+// A population crosses the cut if its velocity moves along the last axis a = D - 1.  Messages hold
+// one plane per crossing velocity, in the library's velocity order.
+template <class S>
+__host__ __device__ constexpr int slab_crossing() {
+    int n = 0;
+    for (int i = 0; i < S::Q; ++i) n += S::c(i, S::D - 1) == 1 ? 1 : 0;
+    return n;
+}
+// Position of velocity i among the crossing velocities with c_a = sign.
+template <class S>
+__host__ __device__ constexpr int slab_slot(int i, int sign) {
+    int n = 0;
+    for (int j = 0; j < i; ++j) n += S::c(j, S::D - 1) == sign ? 1 : 0;
+    return n;
+}
+
+// g points at the first owned cell of a state copy (velocity arrays `pitch` apart, each with one
+// halo plane before the owned planes and one after).  Pack: the populations leaving downward
+// (c_a = -1) from the first owned plane into send_lo, those leaving upward (c_a = +1) from the last
+// owned plane into send_hi.
+template <class S, class T>
+__global__ void k_slab_pack(const T *__restrict__ g, long long pitch, long long plane, int nl, T *__restrict__ send_lo,
+                            T *__restrict__ send_hi) {
+    constexpr int a = S::D - 1;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < plane; x += (long long)gridDim.x * blockDim.x) {
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if constexpr (S::c(i, a) == -1)
+                send_lo[(long long)slab_slot<S>(i, -1) * plane + x] = g[(long long)i * pitch + x];
+            if constexpr (S::c(i, a) == 1)
+                send_hi[(long long)slab_slot<S>(i, 1) * plane + x] = g[(long long)i * pitch + (long long)(nl - 1) * plane + x];
+        });
+    }
+}
+// Unpack: the populations entering from below (c_a = +1, the lower neighbour's send_hi) into the
+// halo plane before the owned planes, those entering from above (c_a = -1) into the one after.
+template <class S, class T>
+__global__ void k_slab_unpack(T *__restrict__ g, long long pitch, long long plane, int nl, const T *__restrict__ recv_lo,
+                              const T *__restrict__ recv_hi) {
+    constexpr int a = S::D - 1;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < plane; x += (long long)gridDim.x * blockDim.x) {
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if constexpr (S::c(i, a) == 1)
+                g[(long long)i * pitch - plane + x] = recv_lo[(long long)slab_slot<S>(i, 1) * plane + x];
+            if constexpr (S::c(i, a) == -1)
+                g[(long long)i * pitch + (long long)nl * plane + x] = recv_hi[(long long)slab_slot<S>(i, -1) * plane + x];
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// writers of BFP16 state (bfp.cuh): every block of 8 cells is encoded together
+// ---------------------------------------------------------------------------------------------
+// One thread per cell with whole warps in every iteration (the loop bound is warp-uniform), so the
+// 8 lanes of a block share its exponent by shuffles; cells past the grid take part as zeros and
+// store nothing.  `value(i, x)` gives the FP32 value of velocity i at cell x.
+template <class S, class F>
+__device__ __forceinline__ void bfp_write_cells(Bfp16 *__restrict__ g, long long cells, long long pitch, F &&value) {
+    uint8_t *__restrict__ ex = bfp_exps<S::Q>(g, pitch);
+    const long long n = (cells + kBfpBlock - 1) / kBfpBlock * kBfpBlock;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n; w0 += stride) {
+        const long long x = w0 + (threadIdx.x & 31);
+        const bool valid = x < cells;
+        float v[S::Q];
+        value(valid ? x : -1, v);
+        static_for<S::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const long long e = (long long)i * pitch + x;
+            const float one[1] = {v[i]};
+            bfp_store_vec<1>(g + e, ex + (e >> 3), one, valid);
+        });
+    }
+}
+
+// g_i = g_i^eq(rho', u', theta') (Sec. 7 initial condition), rounded to FP32 and encoded.
+template <class S>
+__global__ void k_init_equilibrium_bfp(const double *__restrict__ rho, const double *__restrict__ u,
+                                       const double *__restrict__ theta, Bfp16 *__restrict__ g, long long cells,
+                                       long long pitch, SetConsts k) {
+    bfp_write_cells<S>(g, cells, pitch, [&](long long x, float (&v)[S::Q]) {
+        if (x < 0) {
+#pragma unroll
+            for (int i = 0; i < S::Q; ++i) v[i] = 0.f;
+            return;
+        }
+        double uu[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < S::D; ++a) uu[a] = u[(long long)a * cells + x];
+        equilibrium_cell<S, 0>(rho[x], theta[x], uu, k, [&](int i, double val) { v[i] = (float)val; });
+    });
+}
+
+// FP64 [q][cells] -> BFP16 (resume): each value rounded to FP32, then encoded.
+template <class S>
+__global__ void k_import_bfp(const double *__restrict__ in, long long cells, long long pitch, Bfp16 *__restrict__ g) {
+    bfp_write_cells<S>(g, cells, pitch, [&](long long x, float (&v)[S::Q]) {
+#pragma unroll
+        for (int i = 0; i < S::Q; ++i) v[i] = x < 0 ? 0.f : (float)in[(long long)i * cells + x];
+    });
+}
+
+// Sponge damping of a stored BFP16 state (after init_fields): decoded, damped as in the FP32
+// kernel, re-encoded (in place: each warp reads its blocks before it writes them).
+template <class S>
+__global__ void k_sponge_damp_bfp(Bfp16 *__restrict__ g, GridDesc gd, int w, float smax) {
+    const long long cells = (long long)gd.nx * gd.ny * gd.nz;
+    const uint8_t *ex = bfp_exps<S::Q>(g, gd.pitch);
+    bfp_write_cells<S>(g, cells, gd.pitch, [&](long long x, float (&v)[S::Q]) {
+        if (x < 0) {
+#pragma unroll
+            for (int i = 0; i < S::Q; ++i) v[i] = 0.f;
+            return;
+        }
+        const int cx = (int)(x % gd.nx);
+        const long long r = x / gd.nx;
+        const int cy = (int)(r % gd.ny), cz = (int)(r / gd.ny);
+        const float damp = sponge_factor<float>(cx, cy, cz, gd, S::D, w, smax);
+#pragma unroll
+        for (int i = 0; i < S::Q; ++i) v[i] = bfp_load1(g, ex, (long long)i * gd.pitch + x) * damp;
+    });
 }
 
 }  // namespace lee

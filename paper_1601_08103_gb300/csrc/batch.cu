@@ -185,120 +185,14 @@ lee_status launch_one(lee_batch *b, int src_which, cudaStream_t st) {
 
 int full_vec(int storage) { return storage == LEE_STORE_F32 ? 4 : 2; }
 
-std::mutex g_cache_mutex;
-std::map<std::string, std::pair<int, int>> g_cache;
-
-std::string cache_key(const lee_batch *b) {
-    unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the domain extents
-    for (const auto &d : b->doms) {
-        const long long v[2] = {d.nx, d.ny};
-        for (long long x : v)
-            for (int k = 0; k < 8; ++k) {
-                h ^= (unsigned long long)((x >> (8 * k)) & 0xff);
-                h *= 1099511628211ULL;
-            }
-    }
-    std::ostringstream o;
-    o << "batch/set" << b->set << "/st" << b->storage << "/n" << b->count << "/c" << b->total_cells << "/h" << std::hex << h;
-    return o.str();
-}
-
-bool cache_lookup(const std::string &key, int *threads, int *V) {
-    std::lock_guard<std::mutex> lock(g_cache_mutex);
-    auto it = g_cache.find(key);
-    if (it != g_cache.end()) {
-        *threads = it->second.first;
-        *V = it->second.second;
-        return true;
-    }
-    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
-    if (!path || !*path) return false;
-    FILE *f = std::fopen(path, "r");
-    if (!f) return false;
-    char k[512];
-    int t = 0, v = 0;
-    bool found = false;
-    while (std::fscanf(f, "%511s %d %d", k, &t, &v) == 3) {
-        if (key == k) {
-            *threads = t;
-            *V = v;
-            found = true;
-        }
-    }
-    std::fclose(f);
-    if (found) g_cache[key] = {*threads, *V};
-    return found;
-}
-
-void cache_store(const std::string &key, int threads, int V) {
-    std::lock_guard<std::mutex> lock(g_cache_mutex);
-    g_cache[key] = {threads, V};
-    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
-    if (!path || !*path) return;
-    if (FILE *f = std::fopen(path, "a")) {
-        std::fprintf(f, "%s %d %d\n", key.c_str(), threads, V);
-        std::fclose(f);
-    }
-}
-
-lee_status tune(lee_batch *b) {
-    int t = 0, v = 0;
-    const std::string key = cache_key(b);
-    if (cache_lookup(key, &t, &v)) {
-        lee_status s = build_shape(b, t, v);
-        if (s == LEE_OK) b->tuned = true;
-        return s;
-    }
-    const int vf = full_vec(b->storage);
-    const int cand_v[2] = {vf / 2, vf};
-    const int cand_t[3] = {128, 256, 512};
-    float best = 1e30f;
-    int bt = 0, bv = 0;
-    cudaEvent_t e0, e1;
-    BCK(b, cudaEventCreate(&e0), "event");
-    BCK(b, cudaEventCreate(&e1), "event");
-    for (int vi = 0; vi < 2; ++vi) {
-        const int V = cand_v[vi];
-        bool ok = true;
-        for (const auto &d : b->doms) ok = ok && (d.nx % V == 0);
-        if (!ok) continue;
-        for (int ti = 0; ti < 3; ++ti) {
-            lee_status s = build_shape(b, cand_t[ti], V);
-            if (s != LEE_OK) return s;
-            // tuning launches always read the current buffer and write the idle one: no state change
-            for (int w = 0; w < 2; ++w)
-                if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
-            BCK(b, cudaEventRecord(e0, b->st), "event");
-            for (int r = 0; r < 10; ++r)
-                if ((s = launch_one(b, b->cur, b->st)) != LEE_OK) return s;
-            BCK(b, cudaEventRecord(e1, b->st), "event");
-            BCK(b, cudaEventSynchronize(e1), "event sync");
-            float ms = 0.f;
-            BCK(b, cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-            if (ms < best) {
-                best = ms;
-                bt = cand_t[ti];
-                bv = V;
-            }
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (bt == 0) return bfail(b, LEE_ERR_UNSUPPORTED, "no launch shape divides every nx");
-    lee_status s = build_shape(b, bt, bv);
-    if (s != LEE_OK) return s;
-    cache_store(key, bt, bv);
-    b->tuned = true;
-    return LEE_OK;
-}
-
-// Multi-step tiles of 128 columns x at most kBatchTileRows rows (fewer for short domains),
-// listed largest first so that the block scheduler balances the uneven domains.  Measured on
-// GB300 with the four-step kernel on the 96-domain workload (sides multiples of 64): 64 rows 374
-// GLUPS, 48 / 56 / 72 / 80 rows 360-366, 128 rows 367, 256 rows 359.
+// Tile rows of the fused kernel before tuning (on the 96-domain workload, hand-swept with the
+// four-step kernel: 64 rows 374 GLUPS, 48-80 rows 360-366, 128 rows 367, 256 rows 359).
 constexpr int kBatchTileRows = 64;
 
-lee_status build_tb(lee_batch *b, int unit) {
+// Multi-step tiles of 128 columns x `rows` rows (fewer for short domains), in dispatch order
+// `order`: 0 = tiles with the most rows first, so that the block scheduler balances the uneven
+// domains; 1 = domain by domain, rows then columns.  Every shape gives the same bits.
+lee_status build_tb(lee_batch *b, int unit, int rows, int order) {
     cudaError_t e = b->set == LEE_D2Q5 ? prepare_batched_tb<D2Q5>(unit, &b->tb_fn)
                                        : prepare_batched_tb<D2Q5Di>(unit, &b->tb_fn);
     if (e != cudaSuccess) return bfail(b, LEE_ERR_CUDA, std::string("multi-step prepare: ") + cudaGetErrorString(e));
@@ -311,7 +205,7 @@ lee_status build_tb(lee_batch *b, int unit) {
         TbDomain &D = hd[d];
         D.nx = (int)b->doms[d].nx;
         D.ny = (int)b->doms[d].ny;
-        int H = kBatchTileRows;
+        int H = rows;
         const int ny4 = (D.ny + 3) / 4 * 4;
         if (H > ny4) H = ny4;
         D.H = H;
@@ -324,16 +218,199 @@ lee_status build_tb(lee_batch *b, int unit) {
         for (int y0 = 0; y0 < D.ny; y0 += H)
             for (int x0 = 0; x0 < D.nx; x0 += kTbW) tiles.push_back({std::min(H, D.ny - y0), d, x0, y0});
     }
-    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &p, const Tile &q) { return p.rows > q.rows; });
+    if (order == 0)
+        std::stable_sort(tiles.begin(), tiles.end(), [](const Tile &p, const Tile &q) { return p.rows > q.rows; });
     std::vector<int3> ht(tiles.size());
     for (size_t k = 0; k < tiles.size(); ++k) ht[k] = make_int3(tiles[k].d, tiles[k].x0, tiles[k].y0);
-    BCK(b, cudaMalloc(&b->d_tb, sizeof(TbDomain) * hd.size()), "cudaMalloc(multi-step domains)");
-    BCK(b, cudaMalloc(&b->d_tb_tiles, sizeof(int3) * ht.size()), "cudaMalloc(multi-step tiles)");
-    BCK(b, cudaMemcpyAsync(b->d_tb, hd.data(), sizeof(TbDomain) * hd.size(), cudaMemcpyHostToDevice, b->st), "H2D");
-    BCK(b, cudaMemcpyAsync(b->d_tb_tiles, ht.data(), sizeof(int3) * ht.size(), cudaMemcpyHostToDevice, b->st), "H2D");
+    const size_t db = sizeof(TbDomain) * hd.size(), tb = sizeof(int3) * ht.size();
+    if (db > b->d_tb_cap) {
+        cudaFree(b->d_tb);
+        b->d_tb = nullptr;
+        BCK(b, cudaMalloc(&b->d_tb, db), "cudaMalloc(multi-step domains)");
+        b->d_tb_cap = db;
+    }
+    if (tb > b->d_tb_tiles_cap) {
+        cudaFree(b->d_tb_tiles);
+        b->d_tb_tiles = nullptr;
+        BCK(b, cudaMalloc(&b->d_tb_tiles, tb), "cudaMalloc(multi-step tiles)");
+        b->d_tb_tiles_cap = tb;
+    }
+    BCK(b, cudaMemcpyAsync(b->d_tb, hd.data(), db, cudaMemcpyHostToDevice, b->st), "H2D");
+    BCK(b, cudaMemcpyAsync(b->d_tb_tiles, ht.data(), tb, cudaMemcpyHostToDevice, b->st), "H2D");
     BCK(b, cudaStreamSynchronize(b->st), "sync");
     b->tb_blocks = (int)ht.size();
     b->unit = unit;
+    b->tile_rows = rows;
+    b->tile_order = order;
+    drop_graphs(b);
+    return LEE_OK;
+}
+
+// A shape of both kernels: one-step (threads, cells per thread) and fused (steps per launch,
+// tile rows, tile order; steps 1 = no fused kernel).
+struct BatchShape {
+    int threads, V, unit, rows, order;
+    float us;  // measured time per step (0 if set by hand)
+};
+
+lee_status apply_shape(lee_batch *b, const BatchShape &sh) {
+    lee_status s = build_shape(b, sh.threads, sh.V);
+    if (s != LEE_OK) return s;
+    if (sh.unit > 1) return build_tb(b, sh.unit, sh.rows, sh.order);
+    b->unit = 1;
+    drop_graphs(b);
+    return LEE_OK;
+}
+
+std::mutex g_cache_mutex;
+std::map<std::string, BatchShape> g_cache;
+
+std::string cache_key(const lee_batch *b) {
+    unsigned long long h = 1469598103934665603ULL;  // FNV-1a over the domain extents
+    for (const auto &d : b->doms) {
+        const long long v[2] = {d.nx, d.ny};
+        for (long long x : v)
+            for (int k = 0; k < 8; ++k) {
+                h ^= (unsigned long long)((x >> (8 * k)) & 0xff);
+                h *= 1099511628211ULL;
+            }
+    }
+    std::ostringstream o;
+    o << "batch2/set" << b->set << "/st" << b->storage << "/n" << b->count << "/c" << b->total_cells << "/u"
+      << b->unit_fixed << "/h" << std::hex << h;
+    return o.str();
+}
+
+bool cache_lookup(const std::string &key, BatchShape *sh) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *sh = it->second;
+        return true;
+    }
+    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char k[512];
+    BatchShape v{};
+    bool found = false;
+    while (std::fscanf(f, "%511s %d %d %d %d %d %f", k, &v.threads, &v.V, &v.unit, &v.rows, &v.order, &v.us) == 7) {
+        if (key == k) {
+            *sh = v;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_cache[key] = *sh;
+    return found;
+}
+
+void cache_store(const std::string &key, const BatchShape &sh) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    g_cache[key] = sh;
+    const char *path = std::getenv("LEE_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s %d %d %d %d %d %.4f\n", key.c_str(), sh.threads, sh.V, sh.unit, sh.rows, sh.order, sh.us);
+        std::fclose(f);
+    }
+}
+
+// Candidates of the fused kernel's tile rows (multiples of 4, the rows a block's four row warps
+// advance per iteration).
+constexpr int kTuneRows[] = {32, 48, 64, 96, 128};
+
+// The autotuner: times every candidate shape on the batch itself with CUDA events and keeps the
+// one with the least time per step of the whole batch.
+//   one-step kernel: threads per block {128, 256, 512} x cells per thread {V/2, V} (10 launches);
+//   fused kernel (FP32, every nx % 4 == 0): steps per launch {2, 3, 4} (or the one fixed by
+//   LEE_TB_STEPS) x tile rows kTuneRows x tile order {largest first, domain by domain} (6
+//   launches each, after 2 untimed ones).
+// The one-step shape is kept in any case (it runs the steps a fused launch cannot take); the fused
+// shape only if it beats the one-step kernel.  Every tuning launch reads the current buffer and
+// writes the idle one, so the state does not change; every candidate gives the same bits.
+lee_status tune(lee_batch *b) {
+    const std::string key = cache_key(b);
+    BatchShape best{};
+    if (cache_lookup(key, &best)) {
+        lee_status s = apply_shape(b, best);
+        if (s == LEE_OK) {
+            b->tuned = true;
+            b->tuned_us_per_step = best.us;
+        }
+        return s;
+    }
+    const int vf = full_vec(b->storage);
+    const int cand_v[2] = {vf / 2, vf};
+    const int cand_t[3] = {128, 256, 512};
+    float best_us = 1e30f;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0), "event");
+    BCK(b, cudaEventCreate(&e1), "event");
+    auto timed = [&](int launches, bool fused, float *us) -> lee_status {
+        lee_status s = LEE_OK;
+        auto one = [&]() -> lee_status {
+            if (fused) {
+                BCK(b, b->tb_fn(b->buf[b->cur], b->buf[b->cur ^ 1], b->d_tb, b->d_tb_tiles, b->tb_blocks, b->st),
+                    "tuning launch");
+                return LEE_OK;
+            }
+            return launch_one(b, b->cur, b->st);
+        };
+        for (int w = 0; w < 2; ++w)
+            if ((s = one()) != LEE_OK) return s;
+        BCK(b, cudaEventRecord(e0, b->st), "event");
+        for (int r = 0; r < launches; ++r)
+            if ((s = one()) != LEE_OK) return s;
+        BCK(b, cudaEventRecord(e1, b->st), "event");
+        BCK(b, cudaEventSynchronize(e1), "event sync");
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+        *us = ms * 1e3f / (float)launches;
+        return LEE_OK;
+    };
+    for (int vi = 0; vi < 2; ++vi) {
+        const int V = cand_v[vi];
+        bool ok = true;
+        for (const auto &d : b->doms) ok = ok && (d.nx % V == 0);
+        if (!ok) continue;
+        for (int ti = 0; ti < 3; ++ti) {
+            lee_status s = build_shape(b, cand_t[ti], V);
+            if (s != LEE_OK) return s;
+            float us = 0.f;
+            if ((s = timed(10, false, &us)) != LEE_OK) return s;
+            if (us < best_us) {
+                best_us = us;
+                best = BatchShape{cand_t[ti], V, 1, 64, 0, us};
+            }
+        }
+    }
+    if (best.threads == 0) return bfail(b, LEE_ERR_UNSUPPORTED, "no launch shape divides every nx");
+    if (b->fuse_ok && b->unit_fixed != 1) {
+        const BatchShape one = best;
+        for (int unit = 2; unit <= 4; ++unit) {
+            if (b->unit_fixed > 1 && unit != b->unit_fixed) continue;
+            for (int rows : kTuneRows)
+                for (int order = 0; order < 2; ++order) {
+                    lee_status s = build_tb(b, unit, rows, order);
+                    if (s != LEE_OK) return s;
+                    float us = 0.f;
+                    if ((s = timed(6, true, &us)) != LEE_OK) return s;
+                    if (us / unit < best_us) {
+                        best_us = us / unit;
+                        best = BatchShape{one.threads, one.V, unit, rows, order, us / unit};
+                    }
+                }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lee_status s = apply_shape(b, best);
+    if (s != LEE_OK) return s;
+    cache_store(key, best);
+    b->tuned_us_per_step = best_us;
+    b->tuned = true;
     return LEE_OK;
 }
 
@@ -448,10 +525,12 @@ lee_status lee_batch_create(int32_t set, int32_t storage, const lee_batch_domain
     if (const char *ev = std::getenv("LEE_SINGLE_STEP")) {
         if (ev[0] == '1') unit = 1;
     }
-    bool fuse = storage == LEE_STORE_F32 && unit > 1;
-    for (int d = 0; d < count; ++d) fuse = fuse && domains[d].nx % 4 == 0 && domains[d].ny >= 3;
-    if (fuse) {
-        lee_status s2 = build_tb(b, unit);
+    bool fuse_ok = storage == LEE_STORE_F32;
+    for (int d = 0; d < count; ++d) fuse_ok = fuse_ok && domains[d].nx % 4 == 0 && domains[d].ny >= 3;
+    b->fuse_ok = fuse_ok;
+    b->unit_fixed = (std::getenv("LEE_TB_STEPS") || std::getenv("LEE_SINGLE_STEP")) ? unit : 0;
+    if (fuse_ok && unit > 1) {  // the shape before tuning: the given step count, 64-row tiles
+        lee_status s2 = build_tb(b, unit, kBatchTileRows, 0);
         if (s2 != LEE_OK) {
             lee_batch_destroy(b);
             cudaGetLastError();
@@ -604,6 +683,41 @@ lee_status lee_batch_tune(lee_batch *b, int32_t *threads, int32_t *cells_per_thr
     if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
     if (threads) *threads = b->threads;
     if (cells_per_thread) *cells_per_thread = b->V;
+    return LEE_OK;
+}
+
+lee_status lee_batch_tune_shape(lee_batch *b, lee_batch_shape *out) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (!out) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "tune_shape: NULL out");
+    if (!b->tuned && (s = tune(b)) != LEE_OK) return s;
+    out->threads = b->threads;
+    out->cells_per_thread = b->V;
+    out->steps_per_launch = b->unit;
+    out->tile_rows = b->unit > 1 ? b->tile_rows : 0;
+    out->tile_order = b->unit > 1 ? b->tile_order : 0;
+    out->us_per_step = b->tuned_us_per_step;
+    return LEE_OK;
+}
+
+lee_status lee_batch_set_shape(lee_batch *b, const lee_batch_shape *shape) {
+    lee_status s = benter(b);
+    if (s != LEE_OK) return s;
+    if (!shape) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_shape: NULL shape");
+    const int vf = full_vec(b->storage);
+    const BatchShape sh{shape->threads, shape->cells_per_thread, shape->steps_per_launch, shape->tile_rows,
+                        shape->tile_order, 0.f};
+    if ((sh.threads != 128 && sh.threads != 256 && sh.threads != 512) || (sh.V != vf && sh.V != vf / 2))
+        return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_shape: not a candidate one-step shape");
+    for (const auto &d : b->doms)
+        if (d.nx % sh.V) return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_shape: width does not divide nx");
+    if (sh.unit < 1 || sh.unit > 4 || (sh.unit > 1 && !b->fuse_ok))
+        return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_shape: no fused kernel with that step count here");
+    if (sh.unit > 1 && (sh.rows < 4 || sh.rows > 1024 || sh.rows % 4 != 0 || sh.order < 0 || sh.order > 1))
+        return bfail(b, LEE_ERR_INVALID_ARGUMENT, "set_shape: tile rows must be a multiple of 4 in 4..1024, order 0 or 1");
+    if ((s = apply_shape(b, sh)) != LEE_OK) return s;
+    b->tuned_us_per_step = 0.f;
+    b->tuned = true;
     return LEE_OK;
 }
 

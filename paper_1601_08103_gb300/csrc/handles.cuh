@@ -53,6 +53,13 @@ struct lee_lbm {
     // set by LEE_FORCE_SCALAR=1 at create time: one cell per thread in every step kernel, and one
     // step per launch (for comparisons of the vector and packed paths against the scalar one)
     bool force_scalar = false;
+    // LEE_BC_SLAB: nl owned planes of `plane` cells along the cut (last) axis, with one halo plane
+    // before and after them in every velocity array (the state copies start one plane in, see
+    // state()); the four halo messages send_lo, send_hi, recv_lo, recv_hi of `crossing` planes each
+    bool slab = false;
+    long long plane = 0;
+    int nl = 0, crossing = 0;
+    void *halo[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace lee {
@@ -87,9 +94,17 @@ struct lee_batch {
     // a block table
     int unit = 1;
     void *d_tb = nullptr;
-    void *d_tb_tiles = nullptr;  // int3 (domain, x0, y0) per block, largest tiles first
+    void *d_tb_tiles = nullptr;  // int3 (domain, x0, y0) per block, in the tile order below
+    size_t d_tb_cap = 0, d_tb_tiles_cap = 0;
     int tb_blocks = 0;
     lee::BatchedTbFn tb_fn = nullptr;
+    // fused launch shape: tile rows (a multiple of 4) and dispatch order (0: tiles with the most
+    // rows first, 1: domain by domain, row-major); fuse_ok: every domain can take a fused kernel;
+    // unit_fixed: steps per launch fixed by the environment at create time (0: the tuner picks)
+    int tile_rows = 64, tile_order = 0;
+    bool fuse_ok = false;
+    int unit_fixed = 0;
+    float tuned_us_per_step = 0.f;
     // captured graphs, keyed by (starting parity, number of steps); every graph has an even
     // number of steps, so replaying it leaves the buffer parity unchanged
     static constexpr int kMaxGraphSteps = 4096;

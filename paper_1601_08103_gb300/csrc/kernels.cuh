@@ -382,11 +382,15 @@ __device__ __forceinline__ C sponge_factor(int x, int y, int z, const GridDesc &
 // ---------------------------------------------------------------------------------------------
 // One thread's share of a step: V cells starting at chunk `raw` of the grid gd.  All 32 lanes of
 // the warp must call this together (warp shuffles); lanes with raw >= nchunks compute on a clamped
-// chunk and store nothing.
-template <class S, class T, int V, bool OPEN>
+// chunk and store nothing.  CUT (a slab of a larger periodic domain, cut along its last axis: y in
+// 2D, z in 3D): along that axis nothing wraps -- the rows just before and after the grid are read
+// where they lie in memory, in the halo planes the caller keeps there -- and every other axis is
+// periodic.
+template <class S, class T, int V, bool OPEN, bool CUT = false>
 __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, T *__restrict__ dst, const GridDesc &gd,
                                                      const CollideCoef<typename Store<T>::C> &cf,
                                                      const OpenEdge<typename Store<T>::C> &ob, long long raw) {
+    static_assert(!(CUT && OPEN), "a slab is periodic across its cut faces' neighbours");
     using C = typename Store<T>::C;
     const bool active = raw < gd.nchunks;
     const long long chunk = active ? raw : gd.nchunks - 1;
@@ -405,11 +409,11 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
         constexpr int cx = S::c(i, 0), cy = S::c(i, 1), cz = S::c(i, 2);
         int ys = y - cy, zs = z - cz;
         bool row_out = false;
-        if constexpr (cy != 0) {
+        if constexpr (cy != 0 && !(CUT && S::D == 2)) {
             if (ys < 0) { if constexpr (OPEN) row_out = true; else ys += gd.ny; }
             if (ys >= gd.ny) { if constexpr (OPEN) row_out = true; else ys -= gd.ny; }
         }
-        if constexpr (cz != 0) {
+        if constexpr (cz != 0 && !(CUT && S::D == 3)) {
             if (zs < 0) { if constexpr (OPEN) row_out = true; else zs += gd.nz; }
             if (zs >= gd.nz) { if constexpr (OPEN) row_out = true; else zs -= gd.nz; }
         }
@@ -537,11 +541,11 @@ __global__ void __launch_bounds__(1024) k_onchip_1d(T *__restrict__ g, int nx, l
 }
 
 // One fused time step on one grid: one thread per V-cell chunk.
-template <class S, class T, int V, bool OPEN>
+template <class S, class T, int V, bool OPEN, bool CUT = false>
 __global__ void __launch_bounds__(256) k_stream_collide(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
                                                         CollideCoef<typename Store<T>::C> cf,
                                                         OpenEdge<typename Store<T>::C> ob) {
-    stream_collide_chunk<S, T, V, OPEN>(src, dst, gd, cf, ob, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    stream_collide_chunk<S, T, V, OPEN, CUT>(src, dst, gd, cf, ob, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -822,10 +826,40 @@ constexpr int tbk_min_blocks() {
     return K == 3 ? 4 : 3;
 }
 
-template <class S, int K>
-__device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *__restrict__ dst, int nx, int ny,
-                                         long long pitch, int H, const CollideCoef<float> &cf, int x0, int y0,
-                                         float *smem) {
+// Global-memory side of a K-level tile: how level 1 reads S(t) and level K writes S(t+K).  The
+// levels in between are FP32 in shared memory whatever the storage.  A policy gives
+//   Elem        the stored element type;
+//   Vec / One   what a lane's aligned 4-cell load, resp. a single-cell load, leaves in registers
+//               (the loads are issued one iteration ahead and widened only when used);
+//   ld4, ld1    the loads at element index idx of the state copy `base` (pitch between velocity
+//               arrays), cvt4 / cvt1 the widening to FP32;
+//   st4         the store of a lane's 4 cells at idx (every lane of the warp calls it; `store`
+//               false for lanes that own no cells).
+// FP32 storage: plain float4 / float accesses (the stored state is the FP32 state).
+struct TileIoF32 {
+    using Elem = float;
+    using Vec = float4;
+    using One = float;
+    __device__ static __forceinline__ Vec ld4(const float *__restrict__ base, long long, long long idx) {
+        return __ldg(reinterpret_cast<const float4 *>(base + idx));
+    }
+    __device__ static __forceinline__ One ld1(const float *__restrict__ base, long long, long long idx) {
+        return __ldg(base + idx);
+    }
+    __device__ static __forceinline__ void cvt4(const Vec &t, float (&v)[4]) {
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static __forceinline__ float cvt1(const One &t) { return t; }
+    __device__ static __forceinline__ void st4(float *__restrict__ base, long long, long long idx, const float (&v)[4],
+                                               bool store) {
+        if (store) tb_st(base + idx, v);
+    }
+};
+
+template <class S, int K, class IO>
+__device__ __forceinline__ void tbk_tile(const typename IO::Elem *__restrict__ src, typename IO::Elem *__restrict__ dst,
+                                         int nx, int ny, long long pitch, int H, const CollideCoef<float> &cf, int x0,
+                                         int y0, float *smem) {
     static_assert(S::D == 2 && K >= 3 && K <= 4, "deep tiles are 2D with three or four levels");
     constexpr int Q = S::Q;
     // The two 4-row slots of level l (1 .. K-1) form an 8-row circular buffer: row rr of the
@@ -860,9 +894,9 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     for (int e = 0; e < 3; ++e) xh[e] = wrap_x(x0 + o1 - 1 + e);
 
     struct Pre {
-        float4 t[Q];     // row warps: the lane's four cells of velocity i from row a - c_y
-        float edge[Q];   // row warps, lanes 0 and 31: the element the float4 lacks
-        float halo[Q];   // halo warp: the level-1 halo cell's pull of velocity i
+        typename IO::Vec t[Q];     // row warps: the lane's four cells of velocity i from row a - c_y
+        typename IO::One edge[Q];  // row warps, lanes 0 and 31: the element the four cells lack
+        typename IO::One halo[Q];  // halo warp: the level-1 halo cell's pull of velocity i
     };
     Pre pre;
     const int lim1 = y0 + H + K - 2;  // last level-1 row the tile needs
@@ -875,16 +909,16 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
             static_for<Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-                const float *rowp = src + (long long)i * pitch + (long long)rows[1 - cy] * nx;
+                const long long rb = (long long)i * pitch + (long long)rows[1 - cy] * nx;
                 if (!halo_warp) {
-                    pre.t[i] = __ldg(reinterpret_cast<const float4 *>(rowp + xa));
+                    pre.t[i] = IO::ld4(src, pitch, rb + xa);
                     if constexpr (cx == 1) {
-                        if (lane == 0) pre.edge[i] = __ldg(rowp + xedge);
+                        if (lane == 0) pre.edge[i] = IO::ld1(src, pitch, rb + xedge);
                     } else if constexpr (cx == -1) {
-                        if (lane == 31) pre.edge[i] = __ldg(rowp + xedge);
+                        if (lane == 31) pre.edge[i] = IO::ld1(src, pitch, rb + xedge);
                     }
                 } else {
-                    pre.halo[i] = __ldg(rowp + xh[1 - cx]);
+                    pre.halo[i] = IO::ld1(src, pitch, rb + xh[1 - cx]);
                 }
             });
         }
@@ -930,17 +964,18 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
                 static_for<Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     constexpr int cx = S::c(i, 0);
-                    const float4 t = pre.t[i];
+                    float t[kTbV];
+                    IO::cvt4(pre.t[i], t);
                     if constexpr (cx == 0) {
-                        pa[i][0] = t.x; pa[i][1] = t.y; pa[i][2] = t.z; pa[i][3] = t.w;
+                        pa[i][0] = t[0]; pa[i][1] = t[1]; pa[i][2] = t[2]; pa[i][3] = t[3];
                     } else if constexpr (cx == 1) {
-                        float left = __shfl_up_sync(kFull, t.w, 1);
-                        if (lane == 0) left = pre.edge[i];
-                        pa[i][0] = left; pa[i][1] = t.x; pa[i][2] = t.y; pa[i][3] = t.z;
+                        float left = __shfl_up_sync(kFull, t[3], 1);
+                        if (lane == 0) left = IO::cvt1(pre.edge[i]);
+                        pa[i][0] = left; pa[i][1] = t[0]; pa[i][2] = t[1]; pa[i][3] = t[2];
                     } else {
-                        float right = __shfl_down_sync(kFull, t.x, 1);
-                        if (lane == 31) right = pre.edge[i];
-                        pa[i][0] = t.y; pa[i][1] = t.z; pa[i][2] = t.w; pa[i][3] = right;
+                        float right = __shfl_down_sync(kFull, t[0], 1);
+                        if (lane == 31) right = IO::cvt1(pre.edge[i]);
+                        pa[i][0] = t[1]; pa[i][1] = t[2]; pa[i][2] = t[3]; pa[i][3] = right;
                     }
                 });
                 float post[Q][kTbV];
@@ -952,7 +987,7 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
         } else if (4 * k + w1 <= H - 1 + 2 * (K - 1)) {
             float hin[Q][1], hout[Q][1];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) hin[i][0] = pre.halo[i];
+            for (int i = 0; i < Q; ++i) hin[i][0] = IO::cvt1(pre.halo[i]);
             collide_chunk<S, kTbPacked>(hin, hout, cf);
             if (lane < 8 * h1) {
                 float *dst1 = ring(1, (4 * kp + w1) & 7);
@@ -1003,11 +1038,10 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
             pull_level(rows, pb);
             collide_chunk<S, kTbPacked>(pb, post, cf);
             const int d = y0 + 4 * m + warp;
-            if (d < ny && x0 + kTbV * lane < nx) {
-                float *outp = dst + (long long)d * nx + x0 + kTbV * lane;
+            const bool st = d < ny && x0 + kTbV * lane < nx;
+            const long long ob = (long long)d * nx + x0 + kTbV * lane;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) tb_st(outp + (long long)i * pitch, post[i]);
-            }
+            for (int i = 0; i < Q; ++i) IO::st4(dst, pitch, (long long)i * pitch + ob, post[i], st);
         }
     };
     int k = 0;
@@ -1018,13 +1052,12 @@ __device__ __forceinline__ void tbk_tile(const float *__restrict__ src, float *_
     if (k < iters) iteration(k, std::integral_constant<int, 0>{});
 }
 
-template <class S, int K>
-__global__ void __launch_bounds__(kTbkThreads, tbk_min_blocks<K>()) k_stream_collide_kstep(const float *__restrict__ src,
-                                                                                float *__restrict__ dst, int nx,
-                                                                                int ny, long long pitch, int H,
-                                                                                CollideCoef<float> cf) {
+template <class S, int K, class IO = TileIoF32>
+__global__ void __launch_bounds__(kTbkThreads, tbk_min_blocks<K>()) k_stream_collide_kstep(
+    const typename IO::Elem *__restrict__ src, typename IO::Elem *__restrict__ dst, int nx, int ny, long long pitch,
+    int H, CollideCoef<float> cf) {
     extern __shared__ __align__(16) float tb_smem[];
-    tbk_tile<S, K>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
+    tbk_tile<S, K, IO>(src, dst, nx, ny, pitch, H, cf, blockIdx.x * kTbW, blockIdx.y * H, tb_smem);
 }
 
 // K fused steps over many periodic domains: block b works on tile tiles[b] = (domain, x0, y0)
@@ -1036,7 +1069,7 @@ __global__ void __launch_bounds__(kTbkThreads, tbk_min_blocks<K>()) k_stream_col
     extern __shared__ __align__(16) float tb_smem[];
     const int3 tl = tiles[blockIdx.x];
     const TbDomain &D = doms[tl.x];
-    tbk_tile<S, K>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
+    tbk_tile<S, K, TileIoF32>(src + D.offset, dst + D.offset, D.nx, D.ny, D.pitch, D.H, D.cf, tl.y, tl.z, tb_smem);
 }
 
 // Many independent periodic grids (one per domain) advanced by one launch.  Domain d owns the

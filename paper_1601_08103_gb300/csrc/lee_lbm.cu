@@ -146,17 +146,33 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
 // is a multiple of 4; two on periodic 3D FP32 grids of the axis-velocity sets whose width is a
 // multiple of 4; one step otherwise (16-bit storage moves half the bytes and stays on the one-step
 // kernel, which measured faster there).
+//
+// BFP16 storage takes the same multi-step kernels (widths a multiple of its 8-cell block), with the
+// intermediate states in FP32 rather than rounded to the storage: a launch of k steps rounds once,
+// so its results depend on k (deterministically) and stay within the storage error of single
+// steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.
 bool tiled_3d(const lee_lbm *h) {
-    return h->ops->step3d2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
-           h->cfg.nx % 4 == 0;
+    if (!h->ops->step3d2 || h->cfg.bc != LEE_BC_PERIODIC) return false;
+    if (h->cfg.storage == LEE_STORE_BFP16) return h->cfg.nx % 8 == 0;
+    return h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 4 == 0;
 }
 int fused_steps(const lee_lbm *h) {
     if (h->tb_steps <= 1) return 1;
     if (tiled_3d(h)) return 2;
+    if (h->cfg.storage == LEE_STORE_BFP16) {
+        const bool tiled = h->ops->stepk && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.nx % 8 == 0 && h->cfg.ny >= 3;
+        return tiled && h->tb_steps >= 3 ? h->tb_steps : 1;
+    }
     const bool tiled = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
                        h->cfg.nx % 4 == 0 && h->cfg.ny >= 3;
     if (!tiled) return 1;
     return h->tb_steps >= 3 && h->ops->stepk ? h->tb_steps : 2;
+}
+
+// Whether the 1D on-chip path (all steps of a call in one launch) takes this grid.
+bool onchip(const lee_lbm *h) {
+    return h->ops->onchip_1d && h->cfg.storage != LEE_STORE_SPLIT16 && h->cfg.storage != LEE_STORE_BFP16 &&
+           2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
 }
 
 lee_status cuda_fail(lee_lbm *h, cudaError_t e, const char *what) {
@@ -186,6 +202,7 @@ size_t elem_size(int storage) {
     case LEE_STORE_F16:
     case LEE_STORE_BF16: return 2;
     case LEE_STORE_SPLIT16: return 2;  // the non-equilibrium arrays; the moments come on top
+    case LEE_STORE_BFP16: return 2;    // the mantissas; one exponent byte per 8 values on top
     default: return 0;
     }
 }
@@ -193,6 +210,7 @@ size_t elem_size(int storage) {
 // Bytes of one state copy.
 size_t state_bytes(int storage, int D, int Q, long long pitch) {
     if (storage == LEE_STORE_SPLIT16) return (size_t)split_bytes_per_cell(D, Q) * (size_t)pitch;
+    if (storage == LEE_STORE_BFP16) return (size_t)Q * (size_t)pitch * 2 + (size_t)Q * (size_t)pitch / 8;
     return elem_size(storage) * (size_t)Q * (size_t)pitch;
 }
 
@@ -211,6 +229,13 @@ void free_all(lee_lbm *h) {
     cudaFree(h->maxbits);
     cudaFree(h->ghost);
     cudaFree(h->mlp);
+    for (void *p : h->halo) cudaFree(p);
+}
+
+// The first owned cell of state copy `which` (one plane in for a slab, whose halo plane comes
+// first in every velocity array).
+void *state(lee_lbm *h, int which) {
+    return static_cast<char *>(h->buf[which]) + (h->slab ? h->elem * (size_t)h->plane : 0);
 }
 
 // Device address of a host buffer that kernels can use in place: page-locked host memory mapped
@@ -323,7 +348,11 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (cfg->nx > (1LL << 30) || cfg->ny > (1LL << 30) || cfg->nz > (1LL << 30)) return LEE_ERR_INVALID_ARGUMENT;
     const long long cells = cfg->nx * cfg->ny * cfg->nz;
     if (cells >= (1LL << 31)) return LEE_ERR_INVALID_ARGUMENT;
-    if (cfg->bc < LEE_BC_PERIODIC || cfg->bc > LEE_BC_OPEN_LEARNED) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->bc < LEE_BC_PERIODIC || cfg->bc > LEE_BC_SLAB) return LEE_ERR_INVALID_ARGUMENT;
+    if (cfg->bc == LEE_BC_SLAB) {
+        if (o->D < 2) return LEE_ERR_UNSUPPORTED;
+        if (cfg->storage == LEE_STORE_SPLIT16 || cfg->storage == LEE_STORE_BFP16) return LEE_ERR_UNSUPPORTED;
+    }
     if (cfg->bc == LEE_BC_OPEN_SPONGE) {
         if (cfg->sponge_width < 1 || !(cfg->sponge_strength >= 0.0 && cfg->sponge_strength <= 1.0))
             return LEE_ERR_INVALID_ARGUMENT;
@@ -335,6 +364,7 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (cfg->bc == LEE_BC_OPEN_LEARNED && !(o->D == 2 && o->Q == 5)) return LEE_ERR_UNSUPPORTED;
     if (cfg->bc == LEE_BC_OPEN_LEARNED && (cfg->nx < 3 || cfg->ny < 3)) return LEE_ERR_INVALID_ARGUMENT;
     if (cfg->storage == LEE_STORE_SPLIT16 && cfg->bc != LEE_BC_PERIODIC) return LEE_ERR_UNSUPPORTED;
+    if (cfg->storage == LEE_STORE_BFP16 && cfg->bc == LEE_BC_OPEN_LEARNED) return LEE_ERR_UNSUPPORTED;
     if (cfg->store_scale < 0.0 || !std::isfinite(cfg->store_scale)) return LEE_ERR_INVALID_ARGUMENT;
     if (cfg->store_scale > 0.0) {
         int ex = 0;
@@ -350,6 +380,13 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     h->cells = cells;
     h->pitch = (cells + 63) / 64 * 64;
     h->elem = elem_size(cfg->storage);
+    if (cfg->bc == LEE_BC_SLAB) {  // the owned planes and a halo plane on each side
+        h->slab = true;
+        h->plane = o->D == 3 ? cfg->nx * cfg->ny : cfg->nx;
+        h->nl = (int)(o->D == 3 ? cfg->nz : cfg->ny);
+        h->crossing = o->slab_crossing;
+        h->pitch = ((long long)(h->nl + 2) * h->plane + 63) / 64 * 64;
+    }
     h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
     if (const char *ev = std::getenv("LEE_TB_STEPS")) {
         if (ev[0] >= '1' && ev[0] <= '4' && ev[1] == 0) h->tb_steps = ev[0] - '0';
@@ -368,6 +405,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess) e = cudaMalloc(&h->partial, sizeof(double) * kReduceMax * (size_t)h->nblocks);
     if (e == cudaSuccess) e = cudaMalloc(&h->red_out, sizeof(double) * kReduceMax);
     if (e == cudaSuccess) e = cudaMalloc(&h->maxbits, sizeof(unsigned int));
+    for (int k = 0; k < 4 && h->slab && e == cudaSuccess; ++k)
+        e = cudaMalloc(&h->halo[k], h->elem * (size_t)h->crossing * (size_t)h->plane);
     if (e == cudaSuccess && cfg->bc == LEE_BC_OPEN_LEARNED) {
         h->ghost_L = (int)(cfg->nx > cfg->ny ? cfg->nx : cfg->ny);
         e = cudaMalloc(&h->ghost, (cfg->storage == LEE_STORE_F64 ? 8 : 4) * 4 * (size_t)h->ghost_L);
@@ -375,8 +414,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
         e = o->step2_prepare();
     if (e == cudaSuccess && o->stepk_prepare && h->tb_steps >= 3 && cfg->bc == LEE_BC_PERIODIC &&
-        cfg->storage == LEE_STORE_F32)
-        e = o->stepk_prepare(h->tb_steps);
+        (cfg->storage == LEE_STORE_F32 || cfg->storage == LEE_STORE_BFP16))
+        e = o->stepk_prepare(h->tb_steps, cfg->storage);
     if (e == cudaSuccess && h->tb_steps >= 2 && tiled_3d(h)) e = o->step3d2_prepare(cfg->storage);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
@@ -432,7 +471,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
         h->scale = S;
     }
     const SetConsts k = consts_for(h->cfg.set, h->scale);
-    LEE_CK(h, h->ops->init(h->cfg.storage, dr, du, dt, h->buf[0], h->cells, h->pitch, k, h->st), "init kernel");
+    LEE_CK(h, h->ops->init(h->cfg.storage, dr, du, dt, state(h, 0), h->cells, h->pitch, k, h->st), "init kernel");
     if (h->cfg.bc == LEE_BC_OPEN_SPONGE)
         LEE_CK(h, h->ops->sponge_damp(h->cfg.storage, h->buf[0], (int)h->cfg.nx, (int)h->cfg.ny, (int)h->cfg.nz, h->pitch,
                                       h->cfg.sponge_width, h->cfg.sponge_strength, h->st),
@@ -447,6 +486,8 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     lee_status s = enter(h);
     if (s != LEE_OK) return s;
     if (n < 0) return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: n < 0");
+    if (h->slab && n > 1)
+        return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: a slab takes one step per halo exchange (lee_lbm_slab_step)");
     const bool learned = h->cfg.bc == LEE_BC_OPEN_LEARNED;
     if (learned && !h->mlp_ready) return fail(h, LEE_ERR_INVALID_ARGUMENT, "learned boundary: no network installed");
     StepLaunch L{};
@@ -455,7 +496,8 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.ny = (int)h->cfg.ny;
     L.nz = (int)h->cfg.nz;
     L.pitch = h->pitch;
-    L.open = h->cfg.bc != LEE_BC_PERIODIC;
+    L.open = h->cfg.bc != LEE_BC_PERIODIC && h->cfg.bc != LEE_BC_SLAB;
+    L.slab = h->slab ? 1 : 0;
     L.omega = omega_for(h->cfg.storage, h->cfg.tau);
     const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
     fold_coefficients(h->cfg.set, is16, L.omega, L.coefM, L.coefN);
@@ -475,8 +517,8 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         LEE_CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "join event");
     }
     auto launch_step = [&](int from, cudaStream_t st) -> cudaError_t {
-        L.src = h->buf[from];
-        L.dst = h->buf[from ^ 1];
+        L.src = state(h, from);
+        L.dst = state(h, from ^ 1);
         L.stream = st;
         if (!learned) return h->ops->step(L);
         cudaError_t e = cudaEventRecord(h->ev_fork, st);
@@ -495,8 +537,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     };
     int64_t left = n;
     // 1D grids that fit in shared memory: every step in one launch of the on-chip kernel
-    if (h->ops->onchip_1d && n >= 2 && h->cfg.storage != LEE_STORE_SPLIT16 &&
-        2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem) {
+    if (n >= 2 && onchip(h)) {
         L.stream = h->st;
         LEE_CK(h, h->ops->onchip_1d(L, h->buf[h->cur], n), "on-chip 1D launch");
         h->steps += n;
@@ -563,13 +604,13 @@ lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, in
     if (s != LEE_OK) return s;
     const SetConsts k = consts_for(h->cfg.set, h->scale);
     if (on_device) {
-        LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, rho, u, theta, h->st), "moments");
+        LEE_CK(h, h->ops->moments(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, rho, u, theta, h->st), "moments");
         return LEE_OK;
     }
     {
         double *mr = mapped_host(rho), *mu = mapped_host(u), *mt = mapped_host(theta);
         if ((!rho || mr) && (!u || mu) && (!theta || mt)) {  // write the mapped host buffers directly
-            LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, mr, mu, mt, h->st),
+            LEE_CK(h, h->ops->moments(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, mr, mu, mt, h->st),
                    "moments");
             LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
             return LEE_OK;
@@ -577,7 +618,7 @@ lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, in
     }
     if ((s = ensure_fields(h)) != LEE_OK) return s;
     double *fr = h->fields, *fu = h->fields + h->cells, *ft = h->fields + (size_t)(h->D + 1) * h->cells;
-    LEE_CK(h, h->ops->moments(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, fr, fu, ft, h->st), "moments");
+    LEE_CK(h, h->ops->moments(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, fr, fu, ft, h->st), "moments");
     const size_t n = sizeof(double) * (size_t)h->cells;
     if (rho) LEE_CK(h, cudaMemcpyAsync(rho, fr, n, cudaMemcpyDeviceToHost, h->st), "D2H rho");
     if (u) LEE_CK(h, cudaMemcpyAsync(u, fu, n * h->D, cudaMemcpyDeviceToHost, h->st), "D2H u");
@@ -592,7 +633,7 @@ lee_status lee_lbm_reduce(lee_lbm *h, double *out, int32_t on_device) {
     if (!out) return fail(h, LEE_ERR_INVALID_ARGUMENT, "reduce: NULL out");
     const SetConsts k = consts_for(h->cfg.set, h->scale);
     const int nv = h->D + 4;
-    LEE_CK(h, h->ops->reduce_partial(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, h->partial, h->nblocks, h->st),
+    LEE_CK(h, h->ops->reduce_partial(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, h->partial, h->nblocks, h->st),
            "reduce_partial");
     double *dst = on_device ? out : h->red_out;
     const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
@@ -624,7 +665,7 @@ lee_status lee_lbm_get_populations(lee_lbm *h, double *g, int32_t on_device) {
         if ((s = ensure_pops64(h)) != LEE_OK) return s;
         dst = h->pops64;
     }
-    LEE_CK(h, h->ops->export_f64(h->cfg.storage, h->buf[h->cur], h->cells, h->pitch, k, dst, h->st), "export");
+    LEE_CK(h, h->ops->export_f64(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, dst, h->st), "export");
     if (!on_device) {
         LEE_CK(h, cudaMemcpyAsync(g, dst, sizeof(double) * (size_t)h->Q * h->cells, cudaMemcpyDeviceToHost, h->st), "D2H g");
         LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
@@ -645,7 +686,7 @@ lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_devic
         src = h->pops64;
     }
     h->cur = 0;
-    LEE_CK(h, h->ops->import_f64(h->cfg.storage, src, h->cells, h->pitch, k, h->buf[0], h->st), "import");
+    LEE_CK(h, h->ops->import_f64(h->cfg.storage, src, h->cells, h->pitch, k, state(h, 0), h->st), "import");
     h->steps = 0;
     if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
     return LEE_OK;
@@ -669,6 +710,80 @@ lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t npa
     return LEE_OK;
 }
 
+lee_status lee_lbm_slab_info(lee_lbm *h, int32_t *crossing, int64_t *plane_cells, int64_t *bytes) {
+    if (!h) return LEE_ERR_INVALID_ARGUMENT;
+    if (!h->slab) return fail(h, LEE_ERR_INVALID_ARGUMENT, "slab_info: not a slab");
+    if (crossing) *crossing = h->crossing;
+    if (plane_cells) *plane_cells = h->plane;
+    if (bytes) *bytes = (int64_t)(h->elem * (size_t)h->crossing * (size_t)h->plane);
+    return LEE_OK;
+}
+
+lee_status lee_lbm_slab_buffers(lee_lbm *h, void **send_lo, void **send_hi, void **recv_lo, void **recv_hi) {
+    if (!h) return LEE_ERR_INVALID_ARGUMENT;
+    if (!h->slab) return fail(h, LEE_ERR_INVALID_ARGUMENT, "slab_buffers: not a slab");
+    if (send_lo) *send_lo = h->halo[0];
+    if (send_hi) *send_hi = h->halo[1];
+    if (recv_lo) *recv_lo = h->halo[2];
+    if (recv_hi) *recv_hi = h->halo[3];
+    return LEE_OK;
+}
+
+lee_status lee_lbm_slab_pack(lee_lbm *h) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!h->slab) return fail(h, LEE_ERR_INVALID_ARGUMENT, "slab_pack: not a slab");
+    LEE_CK(h, h->ops->slab_pack(h->cfg.storage, state(h, h->cur), h->pitch, h->plane, h->nl, h->halo[0], h->halo[1], h->st),
+           "slab pack");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_slab_unpack(lee_lbm *h) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!h->slab) return fail(h, LEE_ERR_INVALID_ARGUMENT, "slab_unpack: not a slab");
+    LEE_CK(h, h->ops->slab_unpack(h->cfg.storage, state(h, h->cur), h->pitch, h->plane, h->nl, h->halo[2], h->halo[3],
+                                  h->st),
+           "slab unpack");
+    return LEE_OK;
+}
+
+lee_status lee_lbm_slab_step(lee_lbm *const *slabs, int32_t count, int64_t n) {
+    if (!slabs || count < 1 || n < 0) return LEE_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < count; ++k) {
+        lee_lbm *h = slabs[k];
+        if (!h) return LEE_ERR_INVALID_ARGUMENT;
+        if (h->poisoned) return LEE_ERR_POISONED;
+        const lee_lbm *a = slabs[0];
+        const bool same = h->slab && h->cfg.set == a->cfg.set && h->cfg.storage == a->cfg.storage &&
+                          h->cfg.tau == a->cfg.tau && h->cfg.nx == a->cfg.nx && h->plane == a->plane &&
+                          h->device == a->device && h->st == a->st;
+        if (!same)
+            return fail(h, LEE_ERR_INVALID_ARGUMENT,
+                        "slab_step: slabs of one domain (same set, storage, tau, plane, device and stream) only");
+        for (int j = 0; j < k; ++j)
+            if (slabs[j] == h) return fail(h, LEE_ERR_INVALID_ARGUMENT, "slab_step: a slab is listed twice");
+    }
+    const size_t bytes = slabs[0]->elem * (size_t)slabs[0]->crossing * (size_t)slabs[0]->plane;
+    for (int64_t t = 0; t < n; ++t) {
+        lee_status s;
+        for (int k = 0; k < count; ++k)
+            if ((s = lee_lbm_slab_pack(slabs[k])) != LEE_OK) return s;
+        // slab k + 1 lies above slab k, and the last one below the first (periodic domain); each
+        // message is copied into the receiving slab's own buffer, in stream order
+        for (int k = 0; k < count; ++k) {
+            lee_lbm *h = slabs[k], *below = slabs[(k + count - 1) % count], *above = slabs[(k + 1) % count];
+            LEE_CK(h, cudaMemcpyAsync(below->halo[3], h->halo[0], bytes, cudaMemcpyDeviceToDevice, h->st), "halo copy");
+            LEE_CK(h, cudaMemcpyAsync(above->halo[2], h->halo[1], bytes, cudaMemcpyDeviceToDevice, h->st), "halo copy");
+        }
+        for (int k = 0; k < count; ++k)
+            if ((s = lee_lbm_slab_unpack(slabs[k])) != LEE_OK) return s;
+        for (int k = 0; k < count; ++k)
+            if ((s = lee_lbm_step(slabs[k], 1)) != LEE_OK) return s;
+    }
+    return LEE_OK;
+}
+
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
     *steps = h->steps;
@@ -677,9 +792,7 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps) {
 
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps) {
     if (!h || !steps) return LEE_ERR_INVALID_ARGUMENT;
-    const bool onchip = h->ops->onchip_1d && h->cfg.storage != LEE_STORE_SPLIT16 &&
-                        2 * h->elem * (size_t)h->Q * (size_t)h->cfg.nx <= (size_t)kMaxOnchipSmem;
-    *steps = onchip ? 0 : fused_steps(h);
+    *steps = onchip(h) ? 0 : fused_steps(h);
     return LEE_OK;
 }
 

@@ -748,6 +748,7 @@ lee_status lee_lbm_edge_inputs(lee_lbm *h, float *x, float *s) {
     if (!h || !x) return LEE_ERR_INVALID_ARGUMENT;
     if (h->poisoned) return LEE_ERR_POISONED;
     if (h->cfg.set != LEE_D2Q5) return LEE_ERR_UNSUPPORTED;
+    if (h->cfg.storage == LEE_STORE_SPLIT16 || h->cfg.storage == LEE_STORE_BFP16 || h->slab) return LEE_ERR_UNSUPPORTED;
     if (h->cfg.nx < 3 || h->cfg.ny < 3) return LEE_ERR_INVALID_ARGUMENT;
     cudaSetDevice(h->device);
     const int NX = (int)h->cfg.nx, NY = (int)h->cfg.ny;

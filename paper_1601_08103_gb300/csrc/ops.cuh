@@ -26,6 +26,7 @@ struct StepLaunch {
     const void *ghost;   // float (or double for F64) [4][ghost_L], or nullptr
     int ghost_L;
     int force_scalar;    // 1: use the one-cell-per-thread variant (testing)
+    int slab;            // 1: a slab cut along the last axis (halo planes at src/dst -/+ one plane)
     double store_scale;  // storage scale S of the 16-bit and split forms (1 otherwise)
     cudaStream_t stream;
 };
@@ -39,11 +40,12 @@ struct SetOps {
     cudaError_t (*step2)(const StepLaunch &);
     // one-time set-up of the two-step kernel on the current device (outside stream capture)
     cudaError_t (*step2_prepare)();
-    // k = 3 or 4 fused steps per launch on the same grids, and its one-time set-up
+    // k = 3 or 4 fused steps per launch on the same grids (FP32, or BFP16 with nx % 8 == 0), and
+    // its one-time set-up for a storage type
     cudaError_t (*stepk)(const StepLaunch &, int k);
-    cudaError_t (*stepk_prepare)(int k);
-    // two fused steps per launch for the 3D axis-velocity sets (periodic, FP32, nx % 4 == 0;
-    // nullptr for other sets), and its one-time set-up for a storage type
+    cudaError_t (*stepk_prepare)(int k, int storage);
+    // two fused steps per launch for the 3D axis-velocity sets (periodic; FP32 with nx % 4 == 0
+    // or BFP16 with nx % 8 == 0; nullptr for other sets), and its one-time set-up for a storage type
     cudaError_t (*step3d2)(const StepLaunch &);
     cudaError_t (*step3d2_prepare)(int storage);
     // g = g^eq(fields) (fields FP64 on device)
@@ -67,12 +69,21 @@ struct SetOps {
     // border cells of an open 2D grid pulled again with the entering populations L.ghost and
     // collided (after a step with zero-incoming edges); nullptr for 1D/3D sets
     cudaError_t (*edge_fixup)(const StepLaunch &L);
+    // slab halos: packs the populations that leave through the cut faces (first owned plane,
+    // c_last = -1 -> send_lo; last owned plane, c_last = +1 -> send_hi), or unpacks the entering
+    // ones into the halo planes (recv_lo -> plane -1, c_last = +1; recv_hi -> plane nl, c_last = -1).
+    // g: the first owned cell of the state copy; plane: cells per plane; nl: owned planes.
+    cudaError_t (*slab_pack)(int storage, const void *g, long long pitch, long long plane, int nl, void *send_lo,
+                             void *send_hi, cudaStream_t st);
+    cudaError_t (*slab_unpack)(int storage, void *g, long long pitch, long long plane, int nl, const void *recv_lo,
+                               const void *recv_hi, cudaStream_t st);
     // sponge-frame damping of a stored state (after init_fields)
     cudaError_t (*sponge_damp)(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
                                cudaStream_t st);
     // description for lee_velset_info
     int c[27][3];
     int shell[27];
+    int slab_crossing;  // velocities that cross a cut along the last axis, per direction
 };
 
 const SetOps *set_ops(int set);

@@ -84,7 +84,12 @@ struct SetImpl {
         }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
-            k_init_equilibrium<S, T><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, static_cast<T *>(g), cells, pitch, k);
+            if constexpr (std::is_same<T, Bfp16>::value)
+                k_init_equilibrium_bfp<S><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, static_cast<T *>(g), cells,
+                                                                              pitch, k);
+            else
+                k_init_equilibrium<S, T><<<aux_blocks(cells), 256, 0, st>>>(rho, u, theta, static_cast<T *>(g), cells,
+                                                                            pitch, k);
             return cudaGetLastError();
         });
     }
@@ -140,8 +145,38 @@ struct SetImpl {
         }
         return with_storage(storage, [&](auto *tp) {
             using T = std::remove_pointer_t<decltype(tp)>;
-            k_import<S, T><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, k, static_cast<T *>(g));
+            if constexpr (std::is_same<T, Bfp16>::value)
+                k_import_bfp<S><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, static_cast<T *>(g));
+            else
+                k_import<S, T><<<aux_blocks(cells), 256, 0, st>>>(in, cells, pitch, k, static_cast<T *>(g));
             return cudaGetLastError();
+        });
+    }
+    static cudaError_t slab_pack(int storage, const void *g, long long pitch, long long plane, int nl, void *lo,
+                                 void *hi, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) -> cudaError_t {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            if constexpr (std::is_same<T, Bfp16>::value || S::D < 2) {
+                return cudaErrorInvalidValue;
+            } else {
+                k_slab_pack<S, T><<<aux_blocks(plane), 256, 0, st>>>(static_cast<const T *>(g), pitch, plane, nl,
+                                                                     static_cast<T *>(lo), static_cast<T *>(hi));
+                return cudaGetLastError();
+            }
+        });
+    }
+    static cudaError_t slab_unpack(int storage, void *g, long long pitch, long long plane, int nl, const void *lo,
+                                   const void *hi, cudaStream_t st) {
+        return with_storage(storage, [&](auto *tp) -> cudaError_t {
+            using T = std::remove_pointer_t<decltype(tp)>;
+            if constexpr (std::is_same<T, Bfp16>::value || S::D < 2) {
+                return cudaErrorInvalidValue;
+            } else {
+                k_slab_unpack<S, T><<<aux_blocks(plane), 256, 0, st>>>(static_cast<T *>(g), pitch, plane, nl,
+                                                                       static_cast<const T *>(lo),
+                                                                       static_cast<const T *>(hi));
+                return cudaGetLastError();
+            }
         });
     }
     static cudaError_t sponge_damp(int storage, void *g, int nx, int ny, int nz, long long pitch, int w, double smax,
@@ -150,7 +185,10 @@ struct SetImpl {
             using T = std::remove_pointer_t<decltype(tp)>;
             using C = typename Store<T>::C;
             GridDesc gd{nx, ny, nz, nx, (long long)nx * ny * nz, pitch};
-            k_sponge_damp<S, T><<<aux_blocks(gd.nchunks), 256, 0, st>>>(static_cast<T *>(g), gd, w, (C)smax);
+            if constexpr (std::is_same<T, Bfp16>::value)
+                k_sponge_damp_bfp<S><<<aux_blocks(gd.nchunks), 256, 0, st>>>(static_cast<T *>(g), gd, w, (C)smax);
+            else
+                k_sponge_damp<S, T><<<aux_blocks(gd.nchunks), 256, 0, st>>>(static_cast<T *>(g), gd, w, (C)smax);
             return cudaGetLastError();
         });
     }
@@ -158,9 +196,12 @@ struct SetImpl {
         if constexpr (S::D != 1) {
             return cudaErrorInvalidValue;
         } else {
-            return with_storage(L.storage, [&](auto *tp) {
+            return with_storage(L.storage, [&](auto *tp) -> cudaError_t {
                 using T = std::remove_pointer_t<decltype(tp)>;
                 using C = typename Store<T>::C;
+                if constexpr (std::is_same<T, Bfp16>::value) {
+                    return cudaErrorInvalidValue;  // BFP16 runs one launch per step
+                } else {
                 const size_t smem = 2 * sizeof(T) * (size_t)S::Q * (size_t)L.nx;
                 if (smem > (size_t)kMaxOnchipSmem) return cudaErrorInvalidValue;
                 cudaError_t e = cudaFuncSetAttribute(k_onchip_1d<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -199,22 +240,32 @@ struct SetImpl {
                 k_onchip_1d<S, T><<<1, threads, smem, L.stream>>>(static_cast<T *>(g), L.nx, L.pitch, cf, ob, L.open,
                                                                   nsteps);
                 return cudaGetLastError();
+                }
             });
         }
     }
     static cudaError_t step2_prepare() { return two_step_prepare<S>(); }
     static cudaError_t step2(const StepLaunch &L) { return two_step_launch<S>(L); }
-    static cudaError_t stepk_prepare(int k) {
+    // K = 3 or 4 steps per launch: FP32 storage (bit-identical to single steps) or BFP16 storage
+    // (FP32 levels in between, one encoding per launch)
+    static cudaError_t stepk_prepare(int k, int storage) {
+        using B = TileIoBfp<S::Q>;
+        if (storage == LEE_STORE_BFP16)
+            return k == 3 ? kstep_prepare<S, 3, B>() : k == 4 ? kstep_prepare<S, 4, B>() : cudaErrorInvalidValue;
         return k == 3 ? kstep_prepare<S, 3>() : k == 4 ? kstep_prepare<S, 4>() : cudaErrorInvalidValue;
     }
     static cudaError_t stepk(const StepLaunch &L, int k) {
+        using B = TileIoBfp<S::Q>;
+        if (L.storage == LEE_STORE_BFP16)
+            return k == 3 ? kstep_launch<S, 3, B>(L) : k == 4 ? kstep_launch<S, 4, B>(L) : cudaErrorInvalidValue;
         return k == 3 ? kstep_launch<S, 3>(L) : k == 4 ? kstep_launch<S, 4>(L) : cudaErrorInvalidValue;
     }
-    // two steps per launch in 3D (axis-velocity sets, FP32 storage)
+    // two steps per launch in 3D (axis-velocity sets; FP32 storage, or BFP16 with level 1 in FP32)
     static cudaError_t step3d2_prepare(int storage) {
         if constexpr (!axis_only<S>()) {
             return cudaErrorInvalidValue;
         } else {
+            if (storage == LEE_STORE_BFP16) return t3_prepare<S, Bfp16, kT3Rows>();
             return storage == LEE_STORE_F32 ? t3_prepare<S, float, kT3Rows>() : cudaErrorInvalidValue;
         }
     }
@@ -222,6 +273,7 @@ struct SetImpl {
         if constexpr (!axis_only<S>()) {
             return cudaErrorInvalidValue;
         } else {
+            if (L.storage == LEE_STORE_BFP16) return t3_launch<S, Bfp16, kT3Rows>(L);
             return L.storage == LEE_STORE_F32 ? t3_launch<S, float, kT3Rows>(L) : cudaErrorInvalidValue;
         }
     }
@@ -229,9 +281,12 @@ struct SetImpl {
         if constexpr (S::D != 2) {
             return cudaErrorInvalidValue;
         } else {
-            return with_storage(L.storage, [&](auto *tp) {
+            return with_storage(L.storage, [&](auto *tp) -> cudaError_t {
                 using T = std::remove_pointer_t<decltype(tp)>;
                 using C = typename Store<T>::C;
+                if constexpr (std::is_same<T, Bfp16>::value) {
+                    return cudaErrorInvalidValue;  // no learned edge on BFP16 storage
+                } else {
                 GridDesc gd{L.nx, L.ny, 1, L.nx, (long long)L.nx * L.ny, L.pitch};
                 const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
                 OpenEdge<C> ob{0, C(0), static_cast<const C *>(L.ghost), L.ghost_L};
@@ -239,6 +294,7 @@ struct SetImpl {
                 k_edge_fixup<S, T><<<(nb + 127) / 128, 128, 0, L.stream>>>(static_cast<const T *>(L.src),
                                                                           static_cast<T *>(L.dst), gd, cf, ob);
                 return cudaGetLastError();
+                }
             });
         }
     }
@@ -254,6 +310,9 @@ struct SetImpl {
         o.export_f64 = &export_f64;
         o.import_f64 = &import_f64;
         o.sponge_damp = &sponge_damp;
+        o.slab_pack = S::D >= 2 ? &slab_pack : nullptr;
+        o.slab_unpack = S::D >= 2 ? &slab_unpack : nullptr;
+        o.slab_crossing = slab_crossing<S>();
         o.edge_fixup = S::D == 2 ? &edge_fixup : nullptr;
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         o.step2 = S::D == 2 ? &step2 : nullptr;

@@ -8,7 +8,7 @@
 
 namespace lee {
 
-template <class S, class T, int V, bool OPEN>
+template <class S, class T, int V, bool OPEN, bool CUT = false>
 cudaError_t launch_step_v(const StepLaunch &L) {
     using C = typename Store<T>::C;
     GridDesc gd;
@@ -25,8 +25,8 @@ cudaError_t launch_step_v(const StepLaunch &L) {
     ob.ghost = static_cast<const C *>(L.ghost);
     ob.ghost_L = L.ghost_L;
     const long long blocks = (gd.nchunks + 255) / 256;
-    k_stream_collide<S, T, V, OPEN><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
-                                                                              static_cast<T *>(L.dst), gd, cf, ob);
+    k_stream_collide<S, T, V, OPEN, CUT><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
+                                                                                   static_cast<T *>(L.dst), gd, cf, ob);
     return cudaGetLastError();
 }
 
@@ -39,14 +39,53 @@ constexpr int vec_width() {
     return v < 1 ? 1 : v;
 }
 
+// BFP16 storage (bfp.cuh): 8 cells per lane (4 for the 13- and 19-velocity sets, which would
+// need 128 registers at 8) when nx is a multiple of the 8-cell block, one cell per lane otherwise.
+template <class S, int V, bool OPEN>
+cudaError_t launch_step_bfp_v(const StepLaunch &L) {
+    GridDesc gd;
+    gd.nx = L.nx;
+    gd.ny = L.ny;
+    gd.nz = L.nz;
+    gd.nxc = L.nx / V;
+    gd.nchunks = (long long)gd.nxc * L.ny * L.nz;
+    gd.pitch = L.pitch;
+    const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
+    const OpenEdge<float> ob{L.sponge_w, (float)L.sponge_smax, nullptr, 0};
+    const long long blocks = (gd.nchunks + 255) / 256;
+    k_stream_collide_bfp<S, V, OPEN><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const Bfp16 *>(L.src),
+                                                                               static_cast<Bfp16 *>(L.dst), gd, cf, ob);
+    return cudaGetLastError();
+}
+template <class S>
+cudaError_t launch_step_bfp(const StepLaunch &L) {
+    if (L.ghost) return cudaErrorInvalidValue;  // no learned edge on BFP16 storage
+    constexpr int V = S::Q > 9 ? 4 : 8;
+    if (!L.force_scalar && L.nx % kBfpBlock == 0)
+        return L.open ? launch_step_bfp_v<S, V, true>(L) : launch_step_bfp_v<S, V, false>(L);
+    return L.open ? launch_step_bfp_v<S, 1, true>(L) : launch_step_bfp_v<S, 1, false>(L);
+}
+
 template <class S, class T>
 cudaError_t launch_step_t(const StepLaunch &L) {
-    constexpr int V = vec_width<S, T>();
-    if constexpr (V > 1) {
-        if (!L.force_scalar && L.nx % V == 0)
-            return L.open ? launch_step_v<S, T, V, true>(L) : launch_step_v<S, T, V, false>(L);
+    if constexpr (std::is_same<T, Bfp16>::value) {
+        return launch_step_bfp<S>(L);
+    } else {
+        constexpr int V = vec_width<S, T>();
+        if constexpr (S::D >= 2) {
+            if (L.slab) {  // periodic except along the cut, which reads the halo planes
+                if constexpr (V > 1) {
+                    if (!L.force_scalar && L.nx % V == 0) return launch_step_v<S, T, V, false, true>(L);
+                }
+                return launch_step_v<S, T, 1, false, true>(L);
+            }
+        }
+        if constexpr (V > 1) {
+            if (!L.force_scalar && L.nx % V == 0)
+                return L.open ? launch_step_v<S, T, V, true>(L) : launch_step_v<S, T, V, false>(L);
+        }
+        return L.open ? launch_step_v<S, T, 1, true>(L) : launch_step_v<S, T, 1, false>(L);
     }
-    return L.open ? launch_step_v<S, T, 1, true>(L) : launch_step_v<S, T, 1, false>(L);
 }
 
 template <class Fn>
@@ -56,6 +95,7 @@ cudaError_t with_storage(int storage, Fn &&fn) {
     case LEE_STORE_F32: return fn((float *)nullptr);
     case LEE_STORE_F16: return fn((__half *)nullptr);
     case LEE_STORE_BF16: return fn((__nv_bfloat16 *)nullptr);
+    case LEE_STORE_BFP16: return fn((Bfp16 *)nullptr);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -123,12 +163,13 @@ cudaError_t two_step_launch(const StepLaunch &L) {
 
 
 // The same for K steps per launch (K = 3, 4): resident capacity per device, then the launch.
-template <class S, int K>
+// IO: the storage policy of the tile (TileIoF32, or TileIoBfp for BFP16 storage).
+template <class S, int K, class IO>
 int *kstep_capacity() {
     static int cap[64] = {0};
     return cap;
 }
-template <class S, int K>
+template <class S, int K, class IO = TileIoF32>
 cudaError_t kstep_prepare() {
     if constexpr (S::D != 2) {
         return cudaErrorInvalidValue;
@@ -137,34 +178,37 @@ cudaError_t kstep_prepare() {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (kstep_capacity<S, K>()[dev]) return cudaSuccess;
+        if (kstep_capacity<S, K, IO>()[dev]) return cudaSuccess;
         constexpr int smem = tbk_smem_bytes<S, K>();
-        e = cudaFuncSetAttribute(k_stream_collide_kstep<S, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_stream_collide_kstep<S, K, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_kstep<S, K>, kTbkThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_kstep<S, K, IO>, kTbkThreads, smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        kstep_capacity<S, K>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
+        kstep_capacity<S, K, IO>()[dev] = per_sm * sms > 0 ? per_sm * sms : 1;
         return cudaSuccess;
     }
 }
-template <class S, int K>
+template <class S, int K, class IO = TileIoF32>
 cudaError_t kstep_launch(const StepLaunch &L) {
     if constexpr (S::D != 2) {
         return cudaErrorInvalidValue;
     } else {
-        if (L.storage != LEE_STORE_F32 || L.open || L.nx % 4 != 0 || L.ny < 3) return cudaErrorInvalidValue;
+        constexpr bool bfp = std::is_same<typename IO::Elem, Bfp16>::value;
+        if (L.storage != (bfp ? LEE_STORE_BFP16 : LEE_STORE_F32) || L.open || L.nx % (bfp ? kBfpBlock : 4) != 0 ||
+            L.ny < 3)
+            return cudaErrorInvalidValue;
         const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
         constexpr int smem = tbk_smem_bytes<S, K>();
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64 || kstep_capacity<S, K>()[dev] == 0) return cudaErrorNotReady;  // prepare first
+        if (dev < 0 || dev >= 64 || kstep_capacity<S, K, IO>()[dev] == 0) return cudaErrorNotReady;  // prepare first
         // tile height: the smallest multiple of 4 (>= 16) that puts every tile in one resident wave
         const int strips = (L.nx + kTbW - 1) / kTbW;
-        int segs = kstep_capacity<S, K>()[dev] / strips;
+        int segs = kstep_capacity<S, K, IO>()[dev] / strips;
         if (segs < 1) segs = 1;
         int H = (L.ny + segs - 1) / segs;
         H = (H + 3) / 4 * 4;
@@ -173,9 +217,10 @@ cudaError_t kstep_launch(const StepLaunch &L) {
         // No L2 prefetch: it helps the byte-bound two-step kernel on small grids, but this kernel
         // is bound by instruction issue, and the prefetch instructions cost more than they save
         // (measured on GB300, D2Q5 2048^2: 402 GLUPS without, 388 with).
-        k_stream_collide_kstep<S, K><<<grid, kTbkThreads, smem, L.stream>>>(static_cast<const float *>(L.src),
-                                                                     static_cast<float *>(L.dst), L.nx, L.ny, L.pitch,
-                                                                     H, cf);
+        using E = typename IO::Elem;
+        k_stream_collide_kstep<S, K, IO><<<grid, kTbkThreads, smem, L.stream>>>(static_cast<const E *>(L.src),
+                                                                         static_cast<E *>(L.dst), L.nx, L.ny, L.pitch,
+                                                                         H, cf);
         return cudaGetLastError();
     }
 }

@@ -35,7 +35,7 @@
 // 384^3 makes 3 x 48 tiles of 128 x 8 (144 blocks on 152 SMs), each marching all 384 planes.
 #pragma once
 
-#include "kernels.cuh"
+#include "bfp.cuh"
 
 namespace lee {
 
@@ -116,24 +116,66 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
 
     const int iters = HZ + 2;
     // Level-1 inputs of plane p: the lane's vectors, the tile-edge element (lanes 0 and 31) and
-    // the halo cell's pulls; loaded one iteration ahead.
+    // the halo cell's pulls; loaded one iteration ahead.  BFP16 keeps them as loaded (mantissas
+    // and exponent bytes) and decodes them when the next iteration uses them, so that the loads
+    // stay in flight across the barrier.
+    constexpr bool kBfp = std::is_same<T, Bfp16>::value;
     struct In {
         float v[Q][kT3V];
         float edge[Q];
         float h[Q];
     };
-    auto load_in = [&](int p, In &in) {
+    struct InBfp {
+        uint2 m[Q];
+        unsigned e[Q], eu[Q], ee[Q], hu[Q], he[Q];
+    };
+    using Raw = std::conditional_t<kBfp, InBfp, In>;
+    auto load_in = [&](int p, Raw &in) {
         const int pl[3] = {wrap(p - 1, nz), wrap(p, nz), wrap(p + 1, nz)};
         static_for<Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             constexpr int cx = S::c(i, 0), cy = S::c(i, 1), cz = S::c(i, 2);
-            const T *rowp = src + (long long)i * pitch + pl[1 - cz] * plane + (long long)rows[1 - cy] * nx;
-            load_vec<T, kT3V>(rowp + xa, in.v[i]);
-            if constexpr (cx != 0) {
-                if (lane == (cx == 1 ? 0 : 31)) in.edge[i] = Store<T>::load(rowp[xedge]);
+            const long long ri = (long long)i * pitch + pl[1 - cz] * plane + (long long)rows[1 - cy] * nx;
+            if constexpr (kBfp) {
+                const uint8_t *ex = bfp_exps<Q>(src, pitch);
+                in.m[i] = __ldg(reinterpret_cast<const uint2 *>(src + ri + xa));
+                in.e[i] = __ldg(ex + ((ri + xa) >> 3));
+                if constexpr (cx != 0) {
+                    if (lane == (cx == 1 ? 0 : 31)) {
+                        in.eu[i] = __ldg(reinterpret_cast<const unsigned short *>(src + ri + xedge));
+                        in.ee[i] = __ldg(ex + ((ri + xedge) >> 3));
+                    }
+                }
+                in.hu[i] = __ldg(reinterpret_cast<const unsigned short *>(src + ri + xhp[1 - cx]));
+                in.he[i] = __ldg(ex + ((ri + xhp[1 - cx]) >> 3));
+            } else {
+                const T *rowp = src + ri;
+                load_vec<T, kT3V>(rowp + xa, in.v[i]);
+                if constexpr (cx != 0) {
+                    if (lane == (cx == 1 ? 0 : 31)) in.edge[i] = Store<T>::load(rowp[xedge]);
+                }
+                in.h[i] = Store<T>::load(rowp[xhp[1 - cx]]);
             }
-            in.h[i] = Store<T>::load(rowp[xhp[1 - cx]]);
         });
+    };
+    auto widen = [&](const Raw &r, In &o) {
+        if constexpr (kBfp) {
+            static_for<Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = S::c(i, 0);
+                const BfpDec k = bfp_dec(r.e[i]);
+                o.v[i][0] = bfp_lo(r.m[i].x, k);
+                o.v[i][1] = bfp_hi(r.m[i].x, k);
+                o.v[i][2] = bfp_lo(r.m[i].y, k);
+                o.v[i][3] = bfp_hi(r.m[i].y, k);
+                if constexpr (cx != 0) {
+                    if (lane == (cx == 1 ? 0 : 31)) o.edge[i] = bfp_val(r.eu[i], bfp_dec(r.ee[i]));
+                }
+                o.h[i] = bfp_val(r.hu[i], bfp_dec(r.he[i]));
+            });
+        } else {
+            o = r;
+        }
     };
     auto prefetch_plane = [&](int p) {
         if ((lane & 7) == 0) {
@@ -145,12 +187,13 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
             });
         }
     };
-    In nxt;
+    Raw nxt;
     load_in(z0 - 1, nxt);
     for (int k = 0; k < iters; ++k) {
         const int p1 = z0 - 1 + k;
         // ---- level 1: plane p1, row y
-        const In cur = nxt;
+        In cur;
+        widen(nxt, cur);
         if (k + 1 < iters) load_in(p1 + 1, nxt);
         if (k + 2 < iters) prefetch_plane(p1 + 2);
         float pa[Q][kT3V], hin[Q][1];
@@ -179,11 +222,13 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
         float post[Q][kT3V], hout[Q][1];
         collide_chunk<S, true>(pa, post, cf);
         collide_chunk<S, true>(hin, hout, cf);
+        if constexpr (!kBfp) {  // a stored state (BFP16 keeps level 1 in FP32: one rounding per launch)
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
+            for (int i = 0; i < Q; ++i) {
 #pragma unroll
-            for (int e = 0; e < kT3V; ++e) post[i][e] = t3_round<T>(post[i][e]);
-            hout[i][0] = t3_round<T>(hout[i][0]);
+                for (int e = 0; e < kT3V; ++e) post[i][e] = t3_round<T>(post[i][e]);
+                hout[i][0] = t3_round<T>(hout[i][0]);
+            }
         }
         *reinterpret_cast<float4 *>(ring(k % 3, warp, 0) + kT3V * lane) =
             make_float4(post[iPY][0], post[iPY][1], post[iPY][2], post[iPY][3]);
@@ -217,8 +262,16 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
             pb[iMY][0] = b.x; pb[iMY][1] = b.y; pb[iMY][2] = b.z; pb[iMY][3] = b.w;
             float out[Q][kT3V];
             collide_chunk<S, true>(pb, out, cf);
-            if (y < ny && p2 < nz && x0 + kT3V * lane < nx) {
-                T *outp = dst + (long long)p2 * plane + (long long)y * nx + x0 + kT3V * lane;
+            const bool st = y < ny && p2 < nz && x0 + kT3V * lane < nx;
+            const long long oi = (long long)p2 * plane + (long long)y * nx + x0 + kT3V * lane;
+            if constexpr (kBfp) {  // every lane takes part in the block exponents of its pair
+                static_for<Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    const long long e = (long long)i * pitch + oi;
+                    bfp_store_vec<kT3V>(dst + e, bfp_exps<Q>(dst, pitch) + (e >> 3), out[i], st);
+                });
+            } else if (st) {
+                T *outp = dst + oi;
                 static_for<Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     store_vec<T, kT3V>(outp + (long long)i * pitch, out[i]);
@@ -266,6 +319,7 @@ cudaError_t t3_prepare() {
 template <class S, class T, int TY>
 cudaError_t t3_launch(const StepLaunch &L) {
     if (L.open || L.nx % kT3V != 0) return cudaErrorInvalidValue;
+    if (std::is_same<T, Bfp16>::value && L.nx % kBfpBlock != 0) return cudaErrorInvalidValue;  // lane pairs = blocks
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

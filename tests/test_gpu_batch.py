@@ -148,3 +148,59 @@ def test_full_batched_workload(gpu_lib):
         want = oracle.moments("D2Q5", g)[0]
         err = np.linalg.norm(results["graph"][0][d] - want) / np.linalg.norm(want)
         assert err < 5e-5, (d, err)
+
+
+MIXES = [[(nx, ny, t) for nx, ny, t in DOMAINS if nx % 4 == 0],
+         [(256, 256, 0.6), (512, 128, 0.9), (128, 384, 0.55), (1024, 64, 1.1), (64, 200, 0.7)]]
+
+
+@pytest.mark.parametrize("mix", [0, 1])
+def test_autotuner_picks_a_fused_shape_with_the_same_bits(gpu_lib, monkeypatch, mix):
+    """The tuner sweeps the fused kernel (steps per launch x tile rows x tile order) on the batch
+    itself; whatever it picks, and any hand-set shape, gives each domain the bits of single
+    steps."""
+    lee = gpu_lib
+    monkeypatch.delenv("LEE_TB_STEPS", raising=False)
+    monkeypatch.delenv("LEE_SINGLE_STEP", raising=False)
+    doms = MIXES[mix]
+    fields = fields_for(doms, 50 + mix)
+    n = 37
+    want = run_single(lee, "f32", doms, n, fields)
+    with lee.Batch("D2Q5", "f32", doms) as b:
+        for d, f in enumerate(fields):
+            b.init_fields(d, *f)
+        shape = b.tune_shape()
+        assert shape["threads"] in (128, 256, 512) and shape["cells_per_thread"] in (2, 4)
+        assert shape["steps_per_launch"] in (1, 2, 3, 4) and shape["us_per_step"] > 0
+        if shape["steps_per_launch"] > 1:
+            assert shape["tile_rows"] in (32, 48, 64, 96, 128) and shape["tile_order"] in (0, 1)
+        b.step(n, "graph")
+        for d, (nx, ny, _) in enumerate(doms):
+            g = np.empty((5, nx * ny))
+            b.get_populations(d, g)
+            assert np.array_equal(g, want[d]), (mix, d, shape)
+    for steps, rows, order in ((2, 32, 1), (3, 96, 0), (4, 128, 1), (1, 64, 0)):
+        with lee.Batch("D2Q5", "f32", doms) as b:
+            b.set_shape(256, 4, steps, rows, order)
+            assert b.tune_shape()["steps_per_launch"] == steps
+            for d, f in enumerate(fields):
+                b.init_fields(d, *f)
+            b.step(n, "launch")
+            for d, (nx, ny, _) in enumerate(doms):
+                g = np.empty((5, nx * ny))
+                b.get_populations(d, g)
+                assert np.array_equal(g, want[d]), (steps, rows, order, d)
+
+
+def test_set_shape_rejects_bad_shapes(gpu_lib):
+    lee = gpu_lib
+    with lee.Batch("D2Q5", "f32", MIXES[1]) as b:
+        for args in ((100, 4, 4, 64, 0), (256, 3, 4, 64, 0), (256, 4, 5, 64, 0), (256, 4, 4, 62, 0),
+                     (256, 4, 4, 64, 2), (256, 4, 4, 2048, 0)):
+            with pytest.raises(lee.LeeError) as e:
+                b.set_shape(*args)
+            assert e.value.status == lee.LEE_ERR_INVALID_ARGUMENT, args
+    with lee.Batch("D2Q5", "f64", MIXES[1]) as b:  # no fused kernel for FP64 storage
+        with pytest.raises(lee.LeeError):
+            b.set_shape(256, 2, 4, 64, 0)
+        b.set_shape(256, 2, 1, 64, 0)

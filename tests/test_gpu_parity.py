@@ -275,7 +275,7 @@ def oracle_2d_config():
     return fields, _oracle_all_cores("D2Q5", (2048, 2048, 1), 0.6, fields, 1000)
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bfp16", 1e-4)])
 def test_full_size_2d_config_against_oracle(gpu_lib, oracle_2d_config, storage, tol):
     """The 2D configuration itself, through the C ABI in the launch configuration the benchmark
     times (four fused steps per launch in FP32), against the oracle run on all host cores:
@@ -289,7 +289,7 @@ def test_full_size_2d_config_against_oracle(gpu_lib, oracle_2d_config, storage, 
 # Measured storage errors of the 3D configuration against the oracle (not bounds from the paper):
 # each 16-bit store rounds to 11 (FP16) or 8 (BF16) significant bits; the error grows with the
 # number of stores.
-TOL_3D = {"f64": 1e-12, "f32": 1e-5, "f16": 1.5e-3, "bf16": 1.5e-2}
+TOL_3D = {"f64": 1e-12, "f32": 1e-5, "f16": 1.5e-3, "bf16": 1.5e-2, "bfp16": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -301,7 +301,7 @@ def oracle_3d_config():
     return fields, _oracle_all_cores("D3Q7", (384, 384, 384), 0.55, fields, 500)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "bfp16"])
 def test_full_size_3d_config_against_oracle(gpu_lib, oracle_3d_config, storage):
     """The 3D configuration at its stated size and length, through the C ABI in the default
     launch configuration of each storage, against the oracle: FP64 within 1e-12 relative L2 of
@@ -312,6 +312,26 @@ def test_full_size_3d_config_against_oracle(gpu_lib, oracle_3d_config, storage):
     tol = TOL_3D[storage]
     _record("3D D3Q7 384^3 tau=0.55 500 steps", storage, rel_l2(got, want), tol)
     assert_close(got, want, tol, f"3D config rho' ({storage})")
+
+
+@pytest.fixture(scope="module")
+def oracle_2d_8192():
+    """D2Q5 8192^2 with the 2D configuration's pulse and plane waves, 250 steps: fields and the
+    oracle's rho' (about 1.5 minutes on 16 cores)."""
+    fields = inputs.config_2d(8192, seed=2)
+    return fields, _oracle_all_cores("D2Q5", (8192, 8192, 1), 0.6, fields, 250)
+
+
+@pytest.mark.parametrize("storage,tol", [("bfp16", 1e-4), ("f32", 1e-5)])
+def test_2d_grid_beyond_l2_against_oracle(gpu_lib, oracle_2d_8192, storage, tol):
+    """A 2D grid far beyond L2 (D2Q5 8192^2: 2.7 GB of FP32 state, 1.4 GB of BFP16) with the 2D
+    configuration's pulse and plane waves, 250 steps in the default launch configuration (four
+    steps per launch), against the oracle on all host cores: BFP16 within 1e-4, FP32 within 1e-5."""
+    n, steps = 8192, 250
+    fields, want = oracle_2d_8192
+    got = _gpu_rho(gpu_lib, "D2Q5", (n, n, 1), 0.6, storage, fields, steps)
+    _record(f"2D D2Q5 {n}^2 tau=0.6 {steps} steps", storage, rel_l2(got, want), tol)
+    assert_close(got, want, tol, f"2D {n}^2 rho' ({storage})")
 
 
 @pytest.mark.parametrize("name,shape,storage,bc", [("D1Q3", (1024, 1, 1), "f64", "periodic"),
@@ -481,13 +501,17 @@ def test_3d_diatomic_pulse_in_dimensional_units(gpu_lib, storage):
 
 
 @pytest.mark.parametrize("name", SETS)
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "bfp16"])
 @pytest.mark.parametrize("bc", ["periodic", "open_sponge"])
 def test_vector_and_packed_paths_equal_the_scalar_path(gpu_lib, monkeypatch, name, storage, bc):
     """The vector kernels (several cells per thread; FP32 collisions on packed f32x2 pairs; the
     multi-step kernels) spell out every rounding like the one-cell-per-thread kernel, so a run gives
-    the same bits on both paths.  LEE_FORCE_SCALAR=1 at create time selects the scalar path."""
+    the same bits on both paths.  LEE_FORCE_SCALAR=1 at create time selects the scalar path.  BFP16
+    rounds once per launch, so its multi-step kernels are left out here (LEE_TB_STEPS=1); their
+    own test compares them with FP32 steps."""
     lee = gpu_lib
+    if storage == "bfp16":
+        monkeypatch.setenv("LEE_TB_STEPS", "1")
     s = oracle.velset(name)
     shape = shapes_for(s.D, True)[0]
     if bc == "open_sponge" and s.D == 3:

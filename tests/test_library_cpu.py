@@ -85,6 +85,11 @@ def test_velset_info_matches_paper_tables(lib):
     (dict(set_name="D3Q7", shape=(8, 8, 8), bc="open_learned"), lee.LEE_ERR_UNSUPPORTED),
     (dict(set_name="D3Q19", shape=(8, 8, 8), storage="split16", bc="open_zero"), lee.LEE_ERR_UNSUPPORTED),
     (dict(storage="split16", bc="open_sponge", sponge_width=2), lee.LEE_ERR_UNSUPPORTED),
+    (dict(set_name="D1Q3", shape=(64, 1, 1), bc="slab"), lee.LEE_ERR_UNSUPPORTED),   # a slab needs a cut axis
+    (dict(storage="bfp16", bc="slab"), lee.LEE_ERR_UNSUPPORTED),
+    (dict(storage="split16", bc="slab"), lee.LEE_ERR_UNSUPPORTED),
+    (dict(storage="bfp16", bc="open_learned"), lee.LEE_ERR_UNSUPPORTED),
+    (dict(bc="open_sponge", sponge_width=2, storage="bfp16", store_scale=-1.0), lee.LEE_ERR_INVALID_ARGUMENT),
 ])
 def test_create_rejects_bad_configs_on_the_host(lib, kw, status):
     args = dict(set_name="D2Q5", shape=(16, 8, 1), tau=0.6)

@@ -56,14 +56,24 @@ def test_noalloc_matches_handle_reduce_on_two_calls_in_a_row(gpu_lib, name, stor
 
 
 def test_noalloc_rejects_bad_arguments(gpu_lib):
+    """The C entry point's own checks (called directly, past the binding's checks): sizes beyond
+    the fixed scratch, pitch < cells, 16-bit storage without a scale, multi-array storage."""
     import torch
 
+    raw = lee.load()
     g = torch.zeros((5, 64), dtype=torch.float64, device="cuda")
     out = torch.zeros(6, dtype=torch.float64, device="cuda")
-    with pytest.raises(lee.LeeError) as e:
-        lee.lee_reduce_noalloc("D2Q5", "f64", g, 1 << 31, 1 << 31, out)  # more cells than supported
-    assert e.value.status == lee.LEE_ERR_INVALID_ARGUMENT
-    with pytest.raises(lee.LeeError):
-        lee.lee_reduce_noalloc("D2Q5", "f64", g, 64, 32, out)  # pitch < cells
-    with pytest.raises(lee.LeeError):
-        lee.lee_reduce_noalloc("D2Q5", "f16", g, 64, 64, out, store_scale=0.0)  # 16-bit needs S > 0
+    st = torch.cuda.current_stream().cuda_stream
+    d2q5, f64, f16 = lee.SETS["D2Q5"], lee.STORAGE["f64"], lee.STORAGE["f16"]
+    for args in [(d2q5, f64, g.data_ptr(), 1 << 31, 1 << 31, 1.0),  # more cells than the scratch serves
+                 (d2q5, f64, g.data_ptr(), 64, 32, 1.0),              # pitch < cells
+                 (d2q5, f16, g.data_ptr(), 64, 64, 0.0),              # 16-bit storage needs S > 0
+                 (d2q5, lee.STORAGE["split16"], g.data_ptr(), 64, 64, 1.0),
+                 (d2q5, lee.STORAGE["bfp16"], g.data_ptr(), 64, 64, 1.0),
+                 (42, f64, g.data_ptr(), 64, 64, 1.0)]:               # unknown set
+        assert raw.lee_reduce_noalloc(*args, out.data_ptr(), st) == lee.LEE_ERR_INVALID_ARGUMENT, args
+    # and the binding's own checks raise before any launch
+    with pytest.raises(ValueError):
+        lee.lee_reduce_noalloc("D2Q5", "f64", g, 1 << 31, 1 << 31, out)
+    with pytest.raises(ValueError):
+        lee.lee_reduce_noalloc("D2Q5", "f32", g, 64, 64, out)
