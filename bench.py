@@ -394,9 +394,9 @@ def forms_3d():
             sv.moments(r, None, None)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            spl = sv.steps_per_launch
         if storage == "f64":
             ref = r
-            spl = sv.steps_per_launch
         err = float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))
         bpl = 2 * 7 * lee.STORAGE_BYTES[storage]
         out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
@@ -538,6 +538,9 @@ def forms_configs():
                     "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "bytes_per_lup": bpl,
                     "steps_per_launch": spl, "finite": bool(finite)}
         torch.cuda.empty_cache()
+    # the measured FP64 fma rate: the roofline of the FP64 storage forms, whose collision is FP64
+    out["fp64_fma_peak"] = {"tflops": round(lee.lee_probe_fp64_fma(1 << 16) / 1e12, 4),
+                            "how": "8 independent FP64 fma chains per thread, 8 x 256 threads per SM, CUDA events"}
     return out
 
 
@@ -585,7 +588,7 @@ def forms_split():
     u = torch.zeros((3, cells), dtype=torch.float64, device="cuda")
     th = torch.zeros(cells, dtype=torch.float64, device="cuda")
     out, ref = {}, None
-    for storage in ("f64", "f32", "f16", "split16"):
+    for storage in ("f64", "f32", "f16", "split16", "bfp16"):
         with lee.Solver(name, (n, n, n), 0.55, storage=storage, stream=stream) as sv:
             sv.init_fields(rho, u, th)
             sv.step(2)
@@ -606,6 +609,77 @@ def forms_split():
                         "gbs": round(2 * bpc * cells * steps / (ms / 1e3) / 1e9, 1), "bytes_per_cell_copy": bpc,
                         "rel_l2_rho_vs_f64": float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))}
     return {"workload": "3D D3Q19 periodic 256^3, tau=0.55, pulse A=1e-3 w=16, 200 steps", "storage": out}
+
+
+def forms_slab(n: int = 384, steps: int = 100):
+    """Slab decomposition of the 3D configuration's grid (D3Q7 n^3, FP32, tau = 0.55) on one GPU:
+    the domain cut along z into 1, 2 and 4 slabs held in this process, advanced by
+    lee_lbm_slab_step (per step: pack the crossing populations, copy each message into the
+    receiving slab's own buffer, unpack, one one-step launch per slab), against the single-domain
+    one-step run of the same grid (LEE_TB_STEPS=1); results equal bit for bit."""
+    import torch
+
+    import paper_1601_08103_gb300 as lee
+    from paper_1601_08103_gb300 import slab
+
+    stream = torch.cuda.current_stream()
+    cells = n ** 3
+    rho = _device_pulse((n, n, n), 1e-3, 16.0, [n / 2.7] * 3)
+    u = torch.zeros((3, cells), dtype=torch.float64, device="cuda")
+    th = torch.zeros(cells, dtype=torch.float64, device="cuda")
+    out = {}
+
+    def timed(run):
+        run()  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    old = os.environ.get("LEE_TB_STEPS")
+    os.environ["LEE_TB_STEPS"] = "1"
+    try:
+        with lee.Solver("D3Q7", (n, n, n), 0.55, storage="f32", stream=stream) as sv:
+            sv.init_fields(rho, u, th)
+            ms = timed(lambda: sv.step(steps))
+            ref = torch.empty(cells, dtype=torch.float64, device="cuda")
+            sv.init_fields(rho, u, th)
+            sv.step(steps)
+            sv.moments(ref, None, None)
+    finally:
+        if old is None:
+            del os.environ["LEE_TB_STEPS"]
+        else:
+            os.environ["LEE_TB_STEPS"] = old
+    out["single_domain_one_step"] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1), "ms": round(ms, 3)}
+    for count in (1, 2, 4):
+        parts = slab.partition(n, count)
+        slabs = [lee.Solver("D3Q7", (n, n, c), 0.55, storage="f32", bc="slab", stream=stream) for _, c in parts]
+        try:
+            def init():
+                for sv, (z0, c) in zip(slabs, parts):
+                    sl = slice(z0 * n * n, (z0 + c) * n * n)
+                    sv.init_fields(rho[sl].contiguous(), u[:, sl].contiguous(), th[sl].contiguous())
+            init()
+            ms = timed(lambda: lee.lee_lbm_slab_step(slabs, steps))
+            init()
+            lee.lee_lbm_slab_step(slabs, steps)
+            got = torch.empty(cells, dtype=torch.float64, device="cuda")
+            for sv, (z0, c) in zip(slabs, parts):
+                sv.moments(got[z0 * n * n:(z0 + c) * n * n], None, None)
+            torch.cuda.synchronize()
+            crossing, plane, nbytes = slabs[0].slab_info()
+        finally:
+            for sv in slabs:
+                sv.close()
+        out[f"slabs_{count}"] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1), "ms": round(ms, 3),
+                                 "halo_bytes_per_step": 2 * count * nbytes,
+                                 "bit_equal_to_single_domain": bool(torch.equal(got, ref))}
+    return {"workload": f"3D D3Q7 periodic {n}^3 FP32 cut along z, {steps} steps, one GPU (in-process slabs)",
+            "slabs": out}
 
 
 def forms_batched(steps: int = 1000):
@@ -722,6 +796,7 @@ CASES = {
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
     "d2q5_bfp16_8192": ("D2Q5", (8192, 8192, 1), "bfp16", 0.6),
     "d2q5_bfp16": ("D2Q5", (2048, 2048, 1), "bfp16", 0.6),
+    "d2q5_bfp16_4096": ("D2Q5", (4096, 4096, 1), "bfp16", 0.6),
     "d3q7_bfp16": ("D3Q7", (384, 384, 384), "bfp16", 0.55),
     "d3q7_bfp16_256": ("D3Q7", (256, 256, 256), "bfp16", 0.55),
     "d3q19_bfp16": ("D3Q19", (256, 256, 256), "bfp16", 0.55),
@@ -836,6 +911,7 @@ def main(argv=None):
             line["forms_stability"] = forms_stability()
             line["forms_split"] = forms_split()
             line["forms_batched"] = forms_batched()
+            line["forms_slab"] = forms_slab()
             line["forms_learned"] = forms_learned()
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -77,7 +77,11 @@ typedef enum {
  *                 of the cell in the frame (1 .. sponge_width, maximum over axes).
  *   OPEN_LEARNED: 2D five-velocity sets only; the entering population of each edge cell is
  *                 predicted by a small MLP from the 3-cell strip along the inward normal
- *                 (lee_lbm_set_boundary_mlp).
+ *                 (lee_lbm_set_boundary_mlp).  Until a network is installed -- or after
+ *                 lee_lbm_set_boundary_mlp_for_tau found none trained for this tau -- the grid
+ *                 runs the plain buffer instead: OPEN_SPONGE with the configured sponge_width and
+ *                 sponge_strength, or OPEN_ZERO when sponge_width is 0 (lee_lbm_boundary_in_use
+ *                 tells which).
  *   SLAB:         the grid is one slab of a larger periodic domain (Sec. 2.2) cut along its last
  *                 axis (y in 2D, z in 3D; ny resp. nz = the slab's own planes): periodic along the
  *                 other axes, and along the cut the populations that enter come from the
@@ -264,6 +268,18 @@ lee_status lee_lbm_slab_unpack(lee_lbm *h);
  * LEE_ERR_INVALID_ARGUMENT.  Bit for bit the single-domain result of the same storage. */
 lee_status lee_lbm_slab_step(lee_lbm *const *slabs, int32_t count, int64_t n);
 
+/* A boundary network trained at relaxation time trained_tau: installed (as lee_lbm_set_boundary_mlp)
+ * only if |tau - trained_tau| <= tau_tolerance; otherwise the handle runs (or returns to) the
+ * fallback edge of LEE_BC_OPEN_LEARNED.  *installed (may be NULL) receives 1 or 0.
+ * LEE_ERR_INVALID_ARGUMENT for a non-learned handle, a non-finite trained_tau or a negative or
+ * non-finite tolerance. */
+lee_status lee_lbm_set_boundary_mlp_for_tau(lee_lbm *h, const float *params, int64_t nparams, double trained_tau,
+                                            double tau_tolerance, int32_t *installed);
+
+/* The edge treatment the next step runs (lee_bc): the configured one, except that OPEN_LEARNED
+ * reports its fallback (OPEN_SPONGE or OPEN_ZERO) while no network is installed. */
+lee_status lee_lbm_boundary_in_use(lee_lbm *h, int32_t *bc);
+
 /* Number of time steps taken since the last init/set_populations. */
 lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
 
@@ -287,6 +303,13 @@ const char *lee_lbm_last_error(lee_lbm *h);
 
 /* Frees the handle and its device memory.  NULL-safe.  Synchronises the stream first. */
 lee_status lee_lbm_destroy(lee_lbm *h);
+
+/* Measures the current device's FP64 fused multiply-add rate (the paper has no counterpart): 8
+ * blocks of 256 threads per SM each run 8 independent chains of `iters` FP64 fma; *flops_per_s =
+ * 2 x fma count / elapsed time (CUDA events, after a warm-up launch).  The solver's FP64 storage
+ * forms are bounded by this rate rather than by HBM.  Synchronous; allocates 2 KB of scratch.
+ * LEE_ERR_INVALID_ARGUMENT for iters outside 1 .. 2^30 or a NULL output. */
+lee_status lee_probe_fp64_fma(int64_t iters, double *flops_per_s);
 
 /* Test hook for the failure path (the paper has no counterpart).  after >= 0 arms it: of the CUDA
  * calls that solver, batch and network handles check from now on, the (after+1)-th that succeeds

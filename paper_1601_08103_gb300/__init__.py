@@ -84,6 +84,8 @@ _SIGS = {
     "lee_lbm_get_populations": (ctypes.c_int, [_P, _P, _I32]),
     "lee_lbm_set_populations": (ctypes.c_int, [_P, _P, _I32]),
     "lee_lbm_set_boundary_mlp": (ctypes.c_int, [_P, _P, _I64]),
+    "lee_lbm_set_boundary_mlp_for_tau": (ctypes.c_int, [_P, _P, _I64, _D, _D, ctypes.POINTER(_I32)]),
+    "lee_lbm_boundary_in_use": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "lee_lbm_steps_done": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "lee_lbm_slab_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "lee_lbm_slab_buffers": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -98,6 +100,7 @@ _SIGS = {
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
     "lee_reduce_noalloc": (ctypes.c_int, [_I32, _I32, _P, _I64, _I64, _D, _P, _P]),
     "lee_test_inject_cuda_error": (ctypes.c_int, [_I32]),
+    "lee_probe_fp64_fma": (ctypes.c_int, [_I64, ctypes.POINTER(_D)]),
     # include/lee_batch.h
     "lee_batch_create": (ctypes.c_int, [_I32, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
     "lee_batch_init_fields": (ctypes.c_int, [_P, _I32, _P, _P, _P, _I32]),
@@ -310,6 +313,26 @@ def lee_lbm_slab_step(solvers, n: int):
     _check(load().lee_lbm_slab_step(ctypes.cast(arr, _P), len(hs), int(n)), "lee_lbm_slab_step", hs[0])
 
 
+def lee_lbm_set_boundary_mlp_for_tau(h, params, trained_tau: float, tau_tolerance: float = 1e-9) -> bool:
+    """Installs the network if it was trained at this handle's tau (within the tolerance); returns
+    whether it was installed (otherwise the learned edge runs its fallback)."""
+    a, on = _addr(params)
+    if on:
+        raise ValueError("boundary network parameters are read from host memory")
+    n = params.size if hasattr(params, "size") and not callable(params.size) else params.numel()
+    v = _I32()
+    _check(_lib.lee_lbm_set_boundary_mlp_for_tau(h, a, int(n), float(trained_tau), float(tau_tolerance),
+                                                  ctypes.byref(v)), "lee_lbm_set_boundary_mlp_for_tau", h)
+    return bool(v.value)
+
+
+def lee_lbm_boundary_in_use(h) -> str:
+    """Name (a key of BC) of the edge treatment the next step runs."""
+    v = _I32()
+    _check(_lib.lee_lbm_boundary_in_use(h, ctypes.byref(v)), "lee_lbm_boundary_in_use")
+    return {k: name for name, k in BC.items()}[v.value]
+
+
 def lee_lbm_steps_done(h) -> int:
     v = _I64()
     _check(_lib.lee_lbm_steps_done(h, ctypes.byref(v)), "lee_lbm_steps_done")
@@ -393,6 +416,13 @@ def lee_reduce_noalloc(set_name: str, storage: str, g, cells: int, pitch: int, o
                                   float(store_scale), out.data_ptr(), st), "lee_reduce_noalloc")
 
 
+def lee_probe_fp64_fma(iters: int = 1 << 16) -> float:
+    """The current device's measured FP64 fma rate in FLOP/s (see include/lee_lbm.h)."""
+    v = _D()
+    _check(load().lee_probe_fp64_fma(int(iters), ctypes.byref(v)), "lee_probe_fp64_fma")
+    return v.value
+
+
 def lee_test_inject_cuda_error(after: int):
     """Test hook (include/lee_lbm.h): the (after+1)-th successful CUDA call that a handle checks
     from now on is reported as failed, once; -1 disarms."""
@@ -452,6 +482,13 @@ class Solver:
 
     def set_boundary_mlp(self, params):
         lee_lbm_set_boundary_mlp(self.h, params)
+
+    def set_boundary_mlp_for_tau(self, params, trained_tau, tau_tolerance=1e-9) -> bool:
+        return lee_lbm_set_boundary_mlp_for_tau(self.h, params, trained_tau, tau_tolerance)
+
+    @property
+    def boundary_in_use(self) -> str:
+        return lee_lbm_boundary_in_use(self.h)
 
     def slab_info(self):
         return lee_lbm_slab_info(self.h)

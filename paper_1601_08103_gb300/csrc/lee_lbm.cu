@@ -232,6 +232,19 @@ void free_all(lee_lbm *h) {
     for (void *p : h->halo) cudaFree(p);
 }
 
+// A learned edge without a network runs its fallback: the sponge frame of the configuration
+// (zero-incoming edges if its width is 0).
+bool learned_active(const lee_lbm *h) { return h->cfg.bc == LEE_BC_OPEN_LEARNED && h->mlp_ready; }
+bool sponge_active(const lee_lbm *h) {
+    return h->cfg.bc == LEE_BC_OPEN_SPONGE || (h->cfg.bc == LEE_BC_OPEN_LEARNED && !h->mlp_ready && h->cfg.sponge_width > 0);
+}
+
+// Drops the captured step graphs (the launches they hold no longer match the edge treatment).
+void drop_step_graphs(lee_lbm *h) {
+    for (auto &kv : h->exec) cudaGraphExecDestroy(kv.second);
+    h->exec.clear();
+}
+
 // The first owned cell of state copy `which` (one plane in for a slab, whose halo plane comes
 // first in every velocity array).
 void *state(lee_lbm *h, int which) {
@@ -353,7 +366,9 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
         if (o->D < 2) return LEE_ERR_UNSUPPORTED;
         if (cfg->storage == LEE_STORE_SPLIT16 || cfg->storage == LEE_STORE_BFP16) return LEE_ERR_UNSUPPORTED;
     }
-    if (cfg->bc == LEE_BC_OPEN_SPONGE) {
+    // a learned edge may name a sponge frame too: its fallback while no network is installed
+    const bool frame = cfg->bc == LEE_BC_OPEN_SPONGE || (cfg->bc == LEE_BC_OPEN_LEARNED && cfg->sponge_width != 0);
+    if (frame) {
         if (cfg->sponge_width < 1 || !(cfg->sponge_strength >= 0.0 && cfg->sponge_strength <= 1.0))
             return LEE_ERR_INVALID_ARGUMENT;
         for (int a = 0; a < o->D; ++a) {
@@ -472,7 +487,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
     }
     const SetConsts k = consts_for(h->cfg.set, h->scale);
     LEE_CK(h, h->ops->init(h->cfg.storage, dr, du, dt, state(h, 0), h->cells, h->pitch, k, h->st), "init kernel");
-    if (h->cfg.bc == LEE_BC_OPEN_SPONGE)
+    if (sponge_active(h))
         LEE_CK(h, h->ops->sponge_damp(h->cfg.storage, h->buf[0], (int)h->cfg.nx, (int)h->cfg.ny, (int)h->cfg.nz, h->pitch,
                                       h->cfg.sponge_width, h->cfg.sponge_strength, h->st),
                "sponge damp");
@@ -488,8 +503,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     if (n < 0) return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: n < 0");
     if (h->slab && n > 1)
         return fail(h, LEE_ERR_INVALID_ARGUMENT, "step: a slab takes one step per halo exchange (lee_lbm_slab_step)");
-    const bool learned = h->cfg.bc == LEE_BC_OPEN_LEARNED;
-    if (learned && !h->mlp_ready) return fail(h, LEE_ERR_INVALID_ARGUMENT, "learned boundary: no network installed");
+    const bool learned = learned_active(h);
     StepLaunch L{};
     L.storage = h->cfg.storage;
     L.nx = (int)h->cfg.nx;
@@ -501,7 +515,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.omega = omega_for(h->cfg.storage, h->cfg.tau);
     const bool is16 = h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16;
     fold_coefficients(h->cfg.set, is16, L.omega, L.coefM, L.coefN);
-    L.sponge_w = h->cfg.bc == LEE_BC_OPEN_SPONGE ? h->cfg.sponge_width : 0;
+    L.sponge_w = sponge_active(h) ? h->cfg.sponge_width : 0;
     L.sponge_smax = h->cfg.sponge_strength;
     L.ghost = learned ? h->ghost : nullptr;
     L.ghost_L = learned ? h->ghost_L : 0;
@@ -706,7 +720,34 @@ lee_status lee_lbm_set_boundary_mlp(lee_lbm *h, const float *params, int64_t npa
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     cudaFree(tmp);
     LEE_CK(h, e, "install network");
+    if (!h->mlp_ready) drop_step_graphs(h);  // from the fallback edge to the network
     h->mlp_ready = true;
+    return LEE_OK;
+}
+
+lee_status lee_lbm_set_boundary_mlp_for_tau(lee_lbm *h, const float *params, int64_t nparams, double trained_tau,
+                                            double tau_tolerance, int32_t *installed) {
+    lee_status s = enter(h);
+    if (s != LEE_OK) return s;
+    if (!std::isfinite(trained_tau) || !(tau_tolerance >= 0.0) || !std::isfinite(tau_tolerance))
+        return fail(h, LEE_ERR_INVALID_ARGUMENT, "set_boundary_mlp_for_tau: bad trained tau or tolerance");
+    if (std::fabs(h->cfg.tau - trained_tau) > tau_tolerance) {  // not this network: keep or return to the fallback
+        if (h->cfg.bc != LEE_BC_OPEN_LEARNED)
+            return fail(h, LEE_ERR_INVALID_ARGUMENT, "set_boundary_mlp_for_tau: bc is not learned");
+        if (h->mlp_ready) drop_step_graphs(h);
+        h->mlp_ready = false;
+        if (installed) *installed = 0;
+        return LEE_OK;
+    }
+    s = lee_lbm_set_boundary_mlp(h, params, nparams);
+    if (s == LEE_OK && installed) *installed = 1;
+    return s;
+}
+
+lee_status lee_lbm_boundary_in_use(lee_lbm *h, int32_t *bc) {
+    if (!h || !bc) return LEE_ERR_INVALID_ARGUMENT;
+    if (h->cfg.bc != LEE_BC_OPEN_LEARNED) *bc = h->cfg.bc;
+    else *bc = h->mlp_ready ? LEE_BC_OPEN_LEARNED : (h->cfg.sponge_width > 0 ? LEE_BC_OPEN_SPONGE : LEE_BC_OPEN_ZERO);
     return LEE_OK;
 }
 

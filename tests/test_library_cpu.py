@@ -86,6 +86,8 @@ def test_velset_info_matches_paper_tables(lib):
     (dict(set_name="D3Q19", shape=(8, 8, 8), storage="split16", bc="open_zero"), lee.LEE_ERR_UNSUPPORTED),
     (dict(storage="split16", bc="open_sponge", sponge_width=2), lee.LEE_ERR_UNSUPPORTED),
     (dict(set_name="D1Q3", shape=(64, 1, 1), bc="slab"), lee.LEE_ERR_UNSUPPORTED),   # a slab needs a cut axis
+    (dict(bc="open_learned", sponge_width=2, sponge_strength=1.5), lee.LEE_ERR_INVALID_ARGUMENT),  # fallback frame
+    (dict(bc="open_learned", sponge_width=4, shape=(16, 8, 1)), lee.LEE_ERR_INVALID_ARGUMENT),     # frame too wide
     (dict(storage="bfp16", bc="slab"), lee.LEE_ERR_UNSUPPORTED),
     (dict(storage="split16", bc="slab"), lee.LEE_ERR_UNSUPPORTED),
     (dict(storage="bfp16", bc="open_learned"), lee.LEE_ERR_UNSUPPORTED),
