@@ -194,11 +194,12 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  *    run of n steps is n / 4 such launches and n % 4 single steps;
  *  - periodic 3D FP32 grids of D3Q7 and diatomic D3Q7 with nx a multiple of 4 advance two steps
  *    per launch (a z-marching tile; LEE_TB_STEPS=1 keeps one step per launch);
- *  - BFP16 storage on those periodic 2D (four steps, or three with LEE_TB_STEPS=3) and 3D (two
- *    steps) grids with nx a multiple of 8 uses the same kernels, but keeps the intermediate states
- *    in FP32 and encodes only the last one: a launch of k steps equals decoding the state, k FP32
- *    steps and one encoding, bit for bit (LEE_TB_STEPS=1 or 2 keeps one step per launch, which
- *    equals decode, one FP32 step, encode);
+ *  - BFP16 storage on those periodic 2D grids with nx a multiple of 8 uses the same kernels (four
+ *    steps, or three with LEE_TB_STEPS=3), but keeps the intermediate states in FP32 and encodes
+ *    only the last one: a launch of k steps equals decoding the state, k FP32 steps and one
+ *    encoding, bit for bit (LEE_TB_STEPS=1 or 2 keeps one step per launch, which equals decode,
+ *    one FP32 step, encode).  On 3D grids BFP16 runs one step per launch unless LEE_TB_STEPS=2
+ *    asks for the two-step tile (nx a multiple of 8), which is slower there;
  *  - a 1D grid (not BFP16) whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
@@ -287,7 +288,8 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
  * 2..4 (periodic 2D FP32 grids with nx a multiple of 4: that many time steps per launch, the
  * intermediate states kept in shared memory -- temporal blocking; 4 unless LEE_TB_STEPS was set
  * at create time; periodic 3D FP32 D3Q7 and diatomic D3Q7 grids with nx a multiple of 4: 2;
- * BFP16 storage: 3 or 4 in 2D and 2 in 3D on such grids with nx a multiple of 8) or 0 (small 1D
+ * BFP16 storage: 3 or 4 in 2D on such grids with nx a multiple of 8, 2 in 3D only with
+ * LEE_TB_STEPS=2) or 0 (small 1D
  * grid: all steps of a call in one on-chip launch).  All forms give bit-identical results, except
  * that BFP16 rounds its state once per launch (see lee_lbm_step). */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);

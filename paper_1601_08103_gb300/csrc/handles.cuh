@@ -50,9 +50,12 @@ struct lee_lbm {
     // LEE_TB_STEPS=1..4 in the environment at create time overrides it, and LEE_SINGLE_STEP=1
     // sets 1 (for comparisons between the one-, two-, three- and four-step kernels)
     int tb_steps = 4;
+    bool tb_env = false;  // tb_steps came from LEE_TB_STEPS
     // set by LEE_FORCE_SCALAR=1 at create time: one cell per thread in every step kernel, and one
     // step per launch (for comparisons of the vector and packed paths against the scalar one)
     bool force_scalar = false;
+    // LEE_BFP_CELLS=4 or 8 at create time: cells per lane of the BFP16 one-step kernel (0: default)
+    int bfp_cells = 0;
     // LEE_BC_SLAB: nl owned planes of `plane` cells along the cut (last) axis, with one halo plane
     // before and after them in every velocity array (the state copies start one plane in, see
     // state()); the four halo messages send_lo, send_hi, recv_lo, recv_hi of `crossing` planes each

@@ -150,10 +150,12 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
 // BFP16 storage takes the same multi-step kernels (widths a multiple of its 8-cell block), with the
 // intermediate states in FP32 rather than rounded to the storage: a launch of k steps rounds once,
 // so its results depend on k (deterministically) and stay within the storage error of single
-// steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.
+// steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.  In 3D its
+// two-step tile is taken only when LEE_TB_STEPS=2 asks for it: the decoding and encoding make that
+// latency-bound tile slower than the one-step kernel (D3Q7 384^3: 124 against 196 GLUPS).
 bool tiled_3d(const lee_lbm *h) {
     if (!h->ops->step3d2 || h->cfg.bc != LEE_BC_PERIODIC) return false;
-    if (h->cfg.storage == LEE_STORE_BFP16) return h->cfg.nx % 8 == 0;
+    if (h->cfg.storage == LEE_STORE_BFP16) return h->tb_env && h->tb_steps == 2 && h->cfg.nx % 8 == 0;
     return h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 4 == 0;
 }
 int fused_steps(const lee_lbm *h) {
@@ -404,12 +406,18 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     }
     h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
     if (const char *ev = std::getenv("LEE_TB_STEPS")) {
-        if (ev[0] >= '1' && ev[0] <= '4' && ev[1] == 0) h->tb_steps = ev[0] - '0';
+        if (ev[0] >= '1' && ev[0] <= '4' && ev[1] == 0) {
+            h->tb_steps = ev[0] - '0';
+            h->tb_env = true;
+        }
     }
     if (const char *ev = std::getenv("LEE_SINGLE_STEP")) {
         if (ev[0] == '1') h->tb_steps = 1;
     }
     if (const char *ev = std::getenv("LEE_FORCE_SCALAR")) h->force_scalar = ev[0] == '1';
+    if (const char *ev = std::getenv("LEE_BFP_CELLS")) {
+        if ((ev[0] == '4' || ev[0] == '8') && ev[1] == 0) h->bfp_cells = ev[0] - '0';
+    }
     if (h->force_scalar) h->tb_steps = 1;
     h->scale = scaled_storage(cfg->storage) ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -520,6 +528,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.ghost = learned ? h->ghost : nullptr;
     L.ghost_L = learned ? h->ghost_L : 0;
     L.force_scalar = h->force_scalar ? 1 : 0;
+    L.bfp_cells = h->bfp_cells;
     L.store_scale = h->scale;
     // One time step's launches on stream `st`.  Learned edge: the boundary network runs on a side
     // stream while the step runs with zero-incoming edges on `st`; after the join the border

@@ -27,6 +27,7 @@ struct StepLaunch {
     int ghost_L;
     int force_scalar;    // 1: use the one-cell-per-thread variant (testing)
     int slab;            // 1: a slab cut along the last axis (halo planes at src/dst -/+ one plane)
+    int bfp_cells;       // BFP16 one-step kernel: cells per lane (4 or 8), 0 = the default for the set
     double store_scale;  // storage scale S of the 16-bit and split forms (1 otherwise)
     cudaStream_t stream;
 };

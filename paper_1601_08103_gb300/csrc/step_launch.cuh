@@ -40,7 +40,8 @@ constexpr int vec_width() {
 }
 
 // BFP16 storage (bfp.cuh): 8 cells per lane (4 for the 13- and 19-velocity sets, which would
-// need 128 registers at 8) when nx is a multiple of the 8-cell block, one cell per lane otherwise.
+// need 128 registers at 8; LEE_BFP_CELLS=4 or 8 at create time picks either, for comparisons)
+// when nx is a multiple of the 8-cell block, one cell per lane otherwise.
 template <class S, int V, bool OPEN>
 cudaError_t launch_step_bfp_v(const StepLaunch &L) {
     GridDesc gd;
@@ -60,9 +61,11 @@ cudaError_t launch_step_bfp_v(const StepLaunch &L) {
 template <class S>
 cudaError_t launch_step_bfp(const StepLaunch &L) {
     if (L.ghost) return cudaErrorInvalidValue;  // no learned edge on BFP16 storage
-    constexpr int V = S::Q > 9 ? 4 : 8;
-    if (!L.force_scalar && L.nx % kBfpBlock == 0)
-        return L.open ? launch_step_bfp_v<S, V, true>(L) : launch_step_bfp_v<S, V, false>(L);
+    if (!L.force_scalar && L.nx % kBfpBlock == 0) {
+        const int V = L.bfp_cells ? L.bfp_cells : (S::Q > 9 ? 4 : 8);
+        if (V == 4) return L.open ? launch_step_bfp_v<S, 4, true>(L) : launch_step_bfp_v<S, 4, false>(L);
+        return L.open ? launch_step_bfp_v<S, 8, true>(L) : launch_step_bfp_v<S, 8, false>(L);
+    }
     return L.open ? launch_step_bfp_v<S, 1, true>(L) : launch_step_bfp_v<S, 1, false>(L);
 }
 

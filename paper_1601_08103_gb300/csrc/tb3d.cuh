@@ -1,7 +1,9 @@
 // tb3d.cuh -- two time steps per launch (temporal blocking) in 3D for the axis-aligned
 // seven-velocity sets (D3Q7 and diatomic D3Q7, Sec. 8.3), periodic grids with nx % 4 == 0.
-// The solver uses it for FP32 storage; the kernel is written for any storage type, but with
-// FP16/BF16 it measured slower than the one-step kernel (below).
+// The solver uses it for FP32 storage, and for BFP16 storage (bfp.cuh; level 1 then stays in FP32,
+// so a launch rounds to the storage once) when LEE_TB_STEPS=2 asks for it: with FP16/BF16, and with
+// BFP16's decoding and encoding, this latency-bound tile measured slower than the one-step kernel
+// (below; BFP16 on D3Q7 384^3: 124 against 196 GLUPS).
 //
 // A block of W = TY + 2 warps owns a tile of 128 columns x TY rows and marches through planes
 // z0 .. z0 + HZ - 1.  Warp w works on row y = y0 - 1 + w at both levels, lane L on the four
@@ -146,8 +148,10 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
                         in.ee[i] = __ldg(ex + ((ri + xedge) >> 3));
                     }
                 }
-                in.hu[i] = __ldg(reinterpret_cast<const unsigned short *>(src + ri + xhp[1 - cx]));
-                in.he[i] = __ldg(ex + ((ri + xhp[1 - cx]) >> 3));
+                if (lane < 2) {  // the halo cell is used by lanes 0 and 1 only
+                    in.hu[i] = __ldg(reinterpret_cast<const unsigned short *>(src + ri + xhp[1 - cx]));
+                    in.he[i] = __ldg(ex + ((ri + xhp[1 - cx]) >> 3));
+                }
             } else {
                 const T *rowp = src + ri;
                 load_vec<T, kT3V>(rowp + xa, in.v[i]);
@@ -164,14 +168,15 @@ __global__ void __launch_bounds__((TY + 2) * 32, 1) k_stream_collide_3d2(const T
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = S::c(i, 0);
                 const BfpDec k = bfp_dec(r.e[i]);
-                o.v[i][0] = bfp_lo(r.m[i].x, k);
-                o.v[i][1] = bfp_hi(r.m[i].x, k);
-                o.v[i][2] = bfp_lo(r.m[i].y, k);
-                o.v[i][3] = bfp_hi(r.m[i].y, k);
+                const float2 a = bfp_pair(r.m[i].x, k), b = bfp_pair(r.m[i].y, k);
+                o.v[i][0] = a.x;
+                o.v[i][1] = a.y;
+                o.v[i][2] = b.x;
+                o.v[i][3] = b.y;
                 if constexpr (cx != 0) {
                     if (lane == (cx == 1 ? 0 : 31)) o.edge[i] = bfp_val(r.eu[i], bfp_dec(r.ee[i]));
                 }
-                o.h[i] = bfp_val(r.hu[i], bfp_dec(r.he[i]));
+                o.h[i] = lane < 2 ? bfp_val(r.hu[i], bfp_dec(r.he[i])) : 0.f;
             });
         } else {
             o = r;

@@ -108,7 +108,7 @@ def test_default_launch_shapes(gpu_lib, monkeypatch):
     lee = gpu_lib
     monkeypatch.delenv("LEE_TB_STEPS", raising=False)
     monkeypatch.delenv("LEE_SINGLE_STEP", raising=False)
-    for name, shape, want in (("D2Q5", (2048, 2048, 1), 4), ("D2Q5", (260, 64, 1), 1), ("D3Q7", (384, 384, 384), 2),
+    for name, shape, want in (("D2Q5", (2048, 2048, 1), 4), ("D2Q5", (260, 64, 1), 1), ("D3Q7", (384, 384, 384), 1),
                               ("D3Q7", (132, 8, 8), 1), ("D3Q19", (64, 64, 64), 1), ("D1Q3", (1024, 1, 1), 1)):
         with lee.Solver(name, shape, 0.6, storage="bfp16") as sv:
             assert sv.steps_per_launch == want, (name, shape)
