@@ -321,6 +321,16 @@ lee_status lee_probe_fp64_fma(int64_t iters, double *flops_per_s);
  * LEE_ERR_INVALID_ARGUMENT for after < -1. */
 lee_status lee_test_inject_cuda_error(int32_t after);
 
+/* Test hook for the bounded waits of the TMA-fed 3D two-step tile (the paper has no counterpart).
+ * on = 1: every launch of that kernel from now on announces 16 bytes more than its first stage of
+ * inputs receives, so that the wait for that stage runs out after wait_ns nanoseconds (0: the
+ * default limit of one second); the kernel then records the timeout in its handle, lets its copies
+ * in flight land and returns without touching the state.  The handle's next call (or the
+ * synchronisation of the current one) returns LEE_ERR_TIMEOUT and poisons it.  The GPU itself
+ * never faults or hangs.  on = 0 restores normal launches.  Graphs captured while it was on keep
+ * it.  Process-wide; LEE_ERR_INVALID_ARGUMENT for on outside {0, 1} or wait_ns outside 0 .. 10^10. */
+lee_status lee_test_inject_stage_timeout(int32_t on, int64_t wait_ns);
+
 /* The global sums of lee_lbm_reduce (same out[D+4] layout and order, same result bit for bit)
  * for a population field the caller owns, computed WITHOUT ALLOCATING anything.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc (or any routine

@@ -100,6 +100,7 @@ _SIGS = {
     "lee_lbm_destroy": (ctypes.c_int, [_P]),
     "lee_reduce_noalloc": (ctypes.c_int, [_I32, _I32, _P, _I64, _I64, _D, _P, _P]),
     "lee_test_inject_cuda_error": (ctypes.c_int, [_I32]),
+    "lee_test_inject_stage_timeout": (ctypes.c_int, [_I32, _I64]),
     "lee_probe_fp64_fma": (ctypes.c_int, [_I64, ctypes.POINTER(_D)]),
     # include/lee_batch.h
     "lee_batch_create": (ctypes.c_int, [_I32, _I32, _P, _I32, _P, ctypes.POINTER(_P)]),
@@ -427,6 +428,13 @@ def lee_test_inject_cuda_error(after: int):
     """Test hook (include/lee_lbm.h): the (after+1)-th successful CUDA call that a handle checks
     from now on is reported as failed, once; -1 disarms."""
     _check(load().lee_test_inject_cuda_error(int(after)), "lee_test_inject_cuda_error")
+
+
+def lee_test_inject_stage_timeout(on: bool, wait_ns: int = 0):
+    """Test hook (include/lee_lbm.h): launches of the TMA-fed 3D two-step tile announce more bytes
+    than their first stage receives, so that its bounded wait (wait_ns; 0: one second) runs out and
+    the handle reports LEE_ERR_TIMEOUT; on=False restores normal launches."""
+    _check(load().lee_test_inject_stage_timeout(1 if on else 0, int(wait_ns)), "lee_test_inject_stage_timeout")
 
 
 def lee_stability_scan(set_name: str, tau: float, m: int, rho, lam=None, kappa=None, nu=None, delta: float = 1e-6,

@@ -86,7 +86,9 @@ __device__ __forceinline__ float2 bfp_pair(unsigned w, const BfpDec &k) {
 // Inf and NaN order like their bit patterns as unsigned integers).
 __device__ __forceinline__ unsigned bfp_exponent(unsigned maxbits) {
     if (maxbits >= 0x7F800000u) return 255u;
-    const unsigned b = (maxbits >> 23) + ((maxbits & 0x7FFFFFu) >= 8387840u ? 1u : 0u);
+    // the biased exponent, plus 1 when the mantissa field is 8387840 or more (= 2^23 - 768: the
+    // addition carries into the exponent field exactly then)
+    const unsigned b = (maxbits + 768u) >> 23;
     return b > 14u ? b - 14u : 0u;
 }
 // Encoding scale 2^(127 - e) (0 for an all-zero or non-finite block: every u becomes 32768).
@@ -208,10 +210,8 @@ __device__ __forceinline__ void stream_collide_chunk_bfp(const Bfp16 *__restrict
     const bool active = raw < gd.nchunks;
     const long long chunk = active ? raw : gd.nchunks - 1;
     const int lane = threadIdx.x & 31;
-    const int xc = (int)(chunk % gd.nxc);
-    const long long row = chunk / gd.nxc;
-    const int y = (int)(row % gd.ny);
-    const int z = (int)(row / gd.ny);
+    int xc, y, z;
+    chunk_coords(chunk, gd, xc, y, z);
     const int x0 = xc * V;
     const bool has_left = (lane > 0) && (xc > 0);
     const bool has_right = (lane < 31) && (xc < gd.nxc - 1);

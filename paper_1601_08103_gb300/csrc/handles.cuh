@@ -56,6 +56,11 @@ struct lee_lbm {
     bool force_scalar = false;
     // LEE_BFP_CELLS=4 or 8 at create time: cells per lane of the BFP16 one-step kernel (0: default)
     int bfp_cells = 0;
+    // 3D two-step tile: LEE_T3_TMA=1 at create time picks the TMA-fed kernel (0 or -1, unset: the
+    // register-fed one); the TMA-fed kernel records a timed-out stage wait in
+    // wait_host (page-locked, mapped; wait_dev is its device address), read after synchronisations
+    int t3_tma = -1;
+    unsigned *wait_host = nullptr, *wait_dev = nullptr;
     // LEE_BC_SLAB: nl owned planes of `plane` cells along the cut (last) axis, with one halo plane
     // before and after them in every velocity array (the state copies start one plane in, see
     // state()); the four halo messages send_lo, send_hi, recv_lo, recv_hi of `crossing` planes each

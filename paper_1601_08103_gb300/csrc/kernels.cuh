@@ -134,6 +134,25 @@ struct GridDesc {
     long long pitch;    // elements between consecutive velocity arrays
 };
 
+// (xc, y, z) of chunk c = xc + nxc (y + ny z): two 32-bit unsigned divisions while the grid has
+// fewer than 2^32 chunks (a warp-uniform test), 64-bit divisions beyond.
+__device__ __forceinline__ void chunk_coords(long long c, const GridDesc &gd, int &xc, int &y, int &z) {
+    if (gd.nchunks <= 0xFFFFFFFFLL) {
+        const unsigned u = (unsigned)c, nxc = (unsigned)gd.nxc, ny = (unsigned)gd.ny;
+        const unsigned row = u / nxc;
+        xc = (int)(u - row * nxc);
+        const unsigned zz = row / ny;
+        y = (int)(row - zz * ny);
+        z = (int)zz;
+    } else {
+        const long long row = c / gd.nxc;
+        xc = (int)(c - row * gd.nxc);
+        const long long zz = row / gd.ny;
+        y = (int)(row - zz * gd.ny);
+        z = (int)zz;
+    }
+}
+
 // Collision folded into shell space.  With P_s = sum_{i in shell s} g_i and
 // J_s = sum_{i in shell s} c_i g_i, the post-collision population of velocity i in shell t is
 //     g*_i = (1 - w) g_i + sum_s M[t][s] P_s + c_i . (sum_s N[t][s] J_s),     w = 1/tau,
@@ -395,10 +414,8 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
     const bool active = raw < gd.nchunks;
     const long long chunk = active ? raw : gd.nchunks - 1;
     const int lane = threadIdx.x & 31;
-    const int xc = (int)(chunk % gd.nxc);
-    const long long row = chunk / gd.nxc;
-    const int y = (int)(row % gd.ny);
-    const int z = (int)(row / gd.ny);
+    int xc, y, z;
+    chunk_coords(chunk, gd, xc, y, z);
     const int x0 = xc * V;
     const bool has_left = (lane > 0) && (xc > 0);
     const bool has_right = (lane < 31) && (xc < gd.nxc - 1);

@@ -114,6 +114,10 @@ void fold_coefficients(int set, bool scaled, double omega, double M[4][4], doubl
 // Host-side failure injection for tests (lee_test_inject_cuda_error): number of successful
 // checked calls still to pass before one is reported as failed; negative = disarmed.
 std::atomic<int> g_inject_countdown{-1};
+// lee_test_inject_stage_timeout: launches of the TMA-fed 3D tile announce more bytes than their
+// first stage receives (so that its bounded wait runs out), with this wait limit in ns (0: default)
+std::atomic<int> g_inject_stage{0};
+std::atomic<long long> g_stage_wait_ns{0};
 
 cudaError_t checked(cudaError_t e) {
     if (e != cudaSuccess) return e;
@@ -153,8 +157,22 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
 // steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.  In 3D its
 // two-step tile is taken only when LEE_TB_STEPS=2 asks for it: the decoding and encoding make that
 // latency-bound tile slower than the one-step kernel (D3Q7 384^3: 124 against 196 GLUPS).
+//
+// The two-step tile comes in two kernels: fed by per-thread loads (tb3d.cuh; any nx % 4 == 0), the
+// default, or by TMA boxes (tb3d_tma.cuh; grids with nx % 128 == 0, ny a multiple of its 8-row
+// tiles and at least 16, pitch % 128 == 0), taken when LEE_T3_TMA=1 asks for it.  The TMA-fed
+// kernel measured slower on D3Q7 384^3 (FP32 166 against 217 GLUPS, BFP16 105 against 125 for the
+// register-fed tile and 197 for the one-step kernel): with one block of ten computing warps per SM
+// and one barrier per plane it is latency bound, although its stages arrive in time.
+bool tma_tile(const lee_lbm *h) {
+    if (!h->ops->step3d2 || h->cfg.bc != LEE_BC_PERIODIC || h->D != 3 || h->tb_steps < 2) return false;
+    if (h->cfg.storage != LEE_STORE_BFP16 && h->cfg.storage != LEE_STORE_F32) return false;
+    if (!t3t_eligible((int)h->cfg.nx, (int)h->cfg.ny, h->pitch)) return false;
+    return h->t3_tma == 1;
+}
 bool tiled_3d(const lee_lbm *h) {
     if (!h->ops->step3d2 || h->cfg.bc != LEE_BC_PERIODIC) return false;
+    if (tma_tile(h)) return true;
     if (h->cfg.storage == LEE_STORE_BFP16) return h->tb_env && h->tb_steps == 2 && h->cfg.nx % 8 == 0;
     return h->cfg.storage == LEE_STORE_F32 && h->cfg.nx % 4 == 0;
 }
@@ -189,9 +207,24 @@ lee_status cuda_fail(lee_lbm *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail((h), e_, what); \
     } while (0)
 
+// Whether a kernel of this handle recorded a timed-out bounded wait (read without synchronising:
+// the word is set by kernels that already finished, or will be seen after the next sync).
+bool wait_timed_out(const lee_lbm *h) {
+    return h->wait_host && *reinterpret_cast<volatile unsigned *>(h->wait_host) != 0u;
+}
+constexpr const char *kWaitMsg = "3D two-step tile: a bounded wait for a TMA stage ran out";
+
+// Synchronises the handle's stream, then reports a timed-out wait recorded by its kernels.
+#define LEE_SYNC(h)                                                                   \
+    do {                                                                              \
+        LEE_CK((h), cudaStreamSynchronize((h)->st), "sync");                          \
+        if (wait_timed_out(h)) return fail((h), LEE_ERR_TIMEOUT, kWaitMsg);           \
+    } while (0)
+
 lee_status enter(lee_lbm *h) {
     if (!h) return LEE_ERR_INVALID_ARGUMENT;
     if (h->poisoned) return LEE_ERR_POISONED;
+    if (wait_timed_out(h)) return fail(h, LEE_ERR_TIMEOUT, kWaitMsg);
     cudaError_t e = lee::checked(cudaSetDevice(h->device));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     return LEE_OK;
@@ -232,6 +265,8 @@ void free_all(lee_lbm *h) {
     cudaFree(h->ghost);
     cudaFree(h->mlp);
     for (void *p : h->halo) cudaFree(p);
+    if (h->wait_host) cudaFreeHost(h->wait_host);
+    h->wait_host = h->wait_dev = nullptr;
 }
 
 // A learned edge without a network runs its fallback: the sponge frame of the configuration
@@ -302,6 +337,13 @@ const char *lee_status_string(lee_status s) {
 lee_status lee_test_inject_cuda_error(int32_t after) {
     if (after < -1) return LEE_ERR_INVALID_ARGUMENT;
     g_inject_countdown.store(after, std::memory_order_relaxed);
+    return LEE_OK;
+}
+
+lee_status lee_test_inject_stage_timeout(int32_t on, int64_t wait_ns) {
+    if ((on != 0 && on != 1) || wait_ns < 0 || wait_ns > 10000000000LL) return LEE_ERR_INVALID_ARGUMENT;
+    g_inject_stage.store(on, std::memory_order_relaxed);
+    g_stage_wait_ns.store(wait_ns, std::memory_order_relaxed);
     return LEE_OK;
 }
 
@@ -418,6 +460,9 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (const char *ev = std::getenv("LEE_BFP_CELLS")) {
         if ((ev[0] == '4' || ev[0] == '8') && ev[1] == 0) h->bfp_cells = ev[0] - '0';
     }
+    if (const char *ev = std::getenv("LEE_T3_TMA")) {
+        if ((ev[0] == '0' || ev[0] == '1') && ev[1] == 0) h->t3_tma = ev[0] - '0';
+    }
     if (h->force_scalar) h->tb_steps = 1;
     h->scale = scaled_storage(cfg->storage) ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -439,7 +484,14 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && o->stepk_prepare && h->tb_steps >= 3 && cfg->bc == LEE_BC_PERIODIC &&
         (cfg->storage == LEE_STORE_F32 || cfg->storage == LEE_STORE_BFP16))
         e = o->stepk_prepare(h->tb_steps, cfg->storage);
-    if (e == cudaSuccess && h->tb_steps >= 2 && tiled_3d(h)) e = o->step3d2_prepare(cfg->storage);
+    if (e == cudaSuccess && h->tb_steps >= 2 && tiled_3d(h)) e = o->step3d2_prepare(cfg->storage, tma_tile(h) ? 1 : 0);
+    if (e == cudaSuccess && tma_tile(h)) {
+        e = cudaHostAlloc(reinterpret_cast<void **>(&h->wait_host), sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *h->wait_host = 0u;
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->wait_dev), h->wait_host, 0);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, bytes, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -482,7 +534,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
         LEE_CK(h, h->ops->init_maxabs(dr, du, dt, h->cells, consts_for(h->cfg.set, 1.0), h->maxbits, h->st), "init_maxabs");
         unsigned int bits = 0;
         LEE_CK(h, cudaMemcpyAsync(&bits, h->maxbits, sizeof(bits), cudaMemcpyDeviceToHost, h->st), "D2H maxbits");
-        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+        LEE_SYNC(h);
         float m;
         std::memcpy(&m, &bits, sizeof(m));
         double S = 1.0;
@@ -501,7 +553,7 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
                "sponge damp");
     h->cur = 0;
     h->steps = 0;
-    if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    if (!on_device) LEE_SYNC(h);
     return LEE_OK;
 }
 
@@ -530,6 +582,10 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.force_scalar = h->force_scalar ? 1 : 0;
     L.bfp_cells = h->bfp_cells;
     L.store_scale = h->scale;
+    L.t3_tma = tma_tile(h) ? 1 : 0;
+    L.wait_flag = h->wait_dev;
+    L.wait_ns = g_stage_wait_ns.load(std::memory_order_relaxed);
+    L.t3_inject = g_inject_stage.load(std::memory_order_relaxed);
     // One time step's launches on stream `st`.  Learned edge: the boundary network runs on a side
     // stream while the step runs with zero-incoming edges on `st`; after the join the border
     // cells are pulled again with the network's entering populations.  Interior cells never read
@@ -635,7 +691,7 @@ lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, in
         if ((!rho || mr) && (!u || mu) && (!theta || mt)) {  // write the mapped host buffers directly
             LEE_CK(h, h->ops->moments(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, mr, mu, mt, h->st),
                    "moments");
-            LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+            LEE_SYNC(h);
             return LEE_OK;
         }
     }
@@ -646,7 +702,7 @@ lee_status lee_lbm_moments(lee_lbm *h, double *rho, double *u, double *theta, in
     if (rho) LEE_CK(h, cudaMemcpyAsync(rho, fr, n, cudaMemcpyDeviceToHost, h->st), "D2H rho");
     if (u) LEE_CK(h, cudaMemcpyAsync(u, fu, n * h->D, cudaMemcpyDeviceToHost, h->st), "D2H u");
     if (theta) LEE_CK(h, cudaMemcpyAsync(theta, ft, n, cudaMemcpyDeviceToHost, h->st), "D2H theta");
-    LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    LEE_SYNC(h);
     return LEE_OK;
 }
 
@@ -665,7 +721,7 @@ lee_status lee_lbm_reduce(lee_lbm *h, double *out, int32_t on_device) {
     LEE_CK(h, cudaGetLastError(), "reduce_final");
     if (!on_device) {
         LEE_CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->st), "D2H reduce");
-        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+        LEE_SYNC(h);
     }
     return LEE_OK;
 }
@@ -691,7 +747,7 @@ lee_status lee_lbm_get_populations(lee_lbm *h, double *g, int32_t on_device) {
     LEE_CK(h, h->ops->export_f64(h->cfg.storage, state(h, h->cur), h->cells, h->pitch, k, dst, h->st), "export");
     if (!on_device) {
         LEE_CK(h, cudaMemcpyAsync(g, dst, sizeof(double) * (size_t)h->Q * h->cells, cudaMemcpyDeviceToHost, h->st), "D2H g");
-        LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+        LEE_SYNC(h);
     }
     return LEE_OK;
 }
@@ -711,7 +767,7 @@ lee_status lee_lbm_set_populations(lee_lbm *h, const double *g, int32_t on_devic
     h->cur = 0;
     LEE_CK(h, h->ops->import_f64(h->cfg.storage, src, h->cells, h->pitch, k, state(h, 0), h->st), "import");
     h->steps = 0;
-    if (!on_device) LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    if (!on_device) LEE_SYNC(h);
     return LEE_OK;
 }
 
@@ -855,7 +911,7 @@ lee_status lee_lbm_store_scale(lee_lbm *h, double *scale) {
 lee_status lee_lbm_sync(lee_lbm *h) {
     lee_status s = enter(h);
     if (s != LEE_OK) return s;
-    LEE_CK(h, cudaStreamSynchronize(h->st), "sync");
+    LEE_SYNC(h);
     return LEE_OK;
 }
 

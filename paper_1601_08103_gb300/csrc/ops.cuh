@@ -29,6 +29,13 @@ struct StepLaunch {
     int slab;            // 1: a slab cut along the last axis (halo planes at src/dst -/+ one plane)
     int bfp_cells;       // BFP16 one-step kernel: cells per lane (4 or 8), 0 = the default for the set
     double store_scale;  // storage scale S of the 16-bit and split forms (1 otherwise)
+    // 3D two-step tile: 1 = the TMA-fed kernel (tb3d_tma.cuh), 0 = the register-fed one (tb3d.cuh);
+    // for the TMA-fed kernel, where a timed-out stage wait is recorded (device-visible word, or
+    // nullptr), the wait limit in ns (0: one second) and the test injection of such a timeout
+    int t3_tma;
+    unsigned *wait_flag;
+    long long wait_ns;
+    int t3_inject;
     cudaStream_t stream;
 };
 
@@ -47,8 +54,9 @@ struct SetOps {
     cudaError_t (*stepk_prepare)(int k, int storage);
     // two fused steps per launch for the 3D axis-velocity sets (periodic; FP32 with nx % 4 == 0
     // or BFP16 with nx % 8 == 0; nullptr for other sets), and its one-time set-up for a storage type
+    // and kernel (tma = 1: the TMA-fed tile, which also needs t3t_eligible grids)
     cudaError_t (*step3d2)(const StepLaunch &);
-    cudaError_t (*step3d2_prepare)(int storage);
+    cudaError_t (*step3d2_prepare)(int storage, int tma);
     // g = g^eq(fields) (fields FP64 on device)
     cudaError_t (*init)(int storage, const double *rho, const double *u, const double *theta, void *g, long long cells,
                         long long pitch, const SetConsts &k, cudaStream_t st);
@@ -107,6 +115,14 @@ CollideCoef<C> make_coef(double omega, const double M[4][4], const double N[4][4
             cf.N[t][s] = (C)N[t][s];
         }
     return cf;
+}
+
+// Grids the TMA-fed 3D two-step tile (tb3d_tma.cuh) takes: whole 128-column tiles along x, ny a
+// multiple of its kT3tRows-row tiles and at least two of them, and a pitch that keeps the BFP16
+// exponent arrays' strides multiples of 16 bytes.
+constexpr int kT3tRows = 8;
+inline bool t3t_eligible(int nx, int ny, long long pitch) {
+    return nx > 0 && nx % 128 == 0 && ny % kT3tRows == 0 && ny >= 2 * kT3tRows && pitch % 128 == 0;
 }
 
 // Largest dynamic shared memory a block may use on this GPU (227 KB on sm_103a).

@@ -5,6 +5,7 @@
 #include "split.cuh"
 #include "step_launch.cuh"
 #include "tb3d.cuh"
+#include "tb3d_tma.cuh"
 
 namespace lee {
 
@@ -261,10 +262,18 @@ struct SetImpl {
         return k == 3 ? kstep_launch<S, 3>(L) : k == 4 ? kstep_launch<S, 4>(L) : cudaErrorInvalidValue;
     }
     // two steps per launch in 3D (axis-velocity sets; FP32 storage, or BFP16 with level 1 in FP32)
-    static cudaError_t step3d2_prepare(int storage) {
+    // TMA-fed tile instantiations (one block per SM: the BFP16 tile needs 131 registers per thread
+    // without spilling, and 88 per thread, for two blocks, spilled and ran slower): BFP16 with four
+    // stages, FP32 with three
+    using TmaBfp = T3tIoBfp<S::Q>;
+    static cudaError_t step3d2_prepare(int storage, int tma) {
         if constexpr (!axis_only<S>()) {
             return cudaErrorInvalidValue;
         } else {
+            if (tma) {
+                if (storage == LEE_STORE_BFP16) return t3t_prepare<S, TmaBfp, kT3tRows, 4, 1>();
+                return storage == LEE_STORE_F32 ? t3t_prepare<S, T3tIoF32, kT3tRows, 3, 1>() : cudaErrorInvalidValue;
+            }
             if (storage == LEE_STORE_BFP16) return t3_prepare<S, Bfp16, kT3Rows>();
             return storage == LEE_STORE_F32 ? t3_prepare<S, float, kT3Rows>() : cudaErrorInvalidValue;
         }
@@ -273,6 +282,10 @@ struct SetImpl {
         if constexpr (!axis_only<S>()) {
             return cudaErrorInvalidValue;
         } else {
+            if (L.t3_tma) {
+                if (L.storage == LEE_STORE_BFP16) return t3t_launch<S, TmaBfp, kT3tRows, 4, 1>(L);
+                return L.storage == LEE_STORE_F32 ? t3t_launch<S, T3tIoF32, kT3tRows, 3, 1>(L) : cudaErrorInvalidValue;
+            }
             if (L.storage == LEE_STORE_BFP16) return t3_launch<S, Bfp16, kT3Rows>(L);
             return L.storage == LEE_STORE_F32 ? t3_launch<S, float, kT3Rows>(L) : cudaErrorInvalidValue;
         }

@@ -82,10 +82,7 @@ __global__ void __launch_bounds__(128, 5) k_split_step(const float *__restrict__
         const long long raw = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         active = raw < gd.nchunks;
         const long long chunk = active ? raw : gd.nchunks - 1;
-        xc = (int)(chunk % gd.nxc);
-        const long long row = chunk / gd.nxc;
-        y = (int)(row % gd.ny);
-        z = (int)(row / gd.ny);
+        chunk_coords(chunk, gd, xc, y, z);
     }
     const int x0 = xc * V;
     const bool has_left = lane > 0 && xc > 0, has_right = lane < 31 && xc < gd.nxc - 1;
