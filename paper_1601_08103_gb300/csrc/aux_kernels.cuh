@@ -117,18 +117,60 @@ __global__ void k_init_maxabs(const double *__restrict__ rho, const double *__re
     if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(m));
 }
 
-// Border cells of an open 2D grid, after a step that ran with zero-incoming edges: each is pulled
-// again, now with the entering populations of the learned edge (ghost[4][L]: x = 0, x = nx - 1,
-// y = 0, y = ny - 1, indexed along the edge), collided and stored over the zero-incoming result.
-// The pulls follow the fused step's open-edge rules and the collision is collide_cell, so the
-// state equals that of one step run with the ghosts throughout.  One thread per border cell
-// (corners belong to the x-edges).
+// One border cell (x, y) of an open 2D grid, pulled with the entering populations of the learned
+// edge and collided: ghost(e, k) gives the population entering through edge e (0: x = 0, 1:
+// x = nx - 1, 2: y = 0, 3: y = ny - 1) at position k along it.  The pulls follow the fused step's
+// open-edge rules and the collision is collide_cell, so the cell gets what one step run with the
+// ghosts throughout gives it (a corner takes one population from each of its two edges).
+// `pulled(i, xs, ys)` gives the stored value of velocity i at source cell (xs, ys) inside the grid
+// (edge_fixup_cell reads it from src).
+template <class S, class T, class Ghost, class Pulled>
+__device__ __forceinline__ void edge_fixup_cell_from(T *__restrict__ dst, const GridDesc &gd,
+                                                     const CollideCoef<typename Store<T>::C> &cf, Ghost ghost,
+                                                     Pulled pulled, int x, int y) {
+    static_assert(S::D == 2, "border cells of 2D grids");
+    using C = typename Store<T>::C;
+    const int nx = gd.nx, ny = gd.ny;
+    C pull[S::Q][1], post[S::Q][1];
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
+        const int xs = x - cx, ys = y - cy;
+        C v = C(0);
+        if (ys < 0 || ys >= ny) {  // enters through the bottom (c_y = +1) or top edge
+            if (cx == 0) v = ghost(cy == 1 ? 2 : 3, x);
+        } else if (xs < 0) {  // through the left edge
+            if (cy == 0) v = ghost(0, y);
+        } else if (xs >= nx) {  // through the right edge
+            if (cy == 0) v = ghost(1, y);
+        } else {
+            v = pulled(i, xs, ys);
+        }
+        pull[i][0] = v;
+    });
+    collide_cell<S, 0>(pull, post, cf);
+#pragma unroll
+    for (int i = 0; i < S::Q; ++i) dst[(long long)i * gd.pitch + (long long)y * nx + x] = Store<T>::make(post[i][0]);
+}
+template <class S, class T, class Ghost>
+__device__ __forceinline__ void edge_fixup_cell(const T *__restrict__ src, T *__restrict__ dst, const GridDesc &gd,
+                                                const CollideCoef<typename Store<T>::C> &cf, Ghost ghost, int x,
+                                                int y) {
+    edge_fixup_cell_from<S, T>(dst, gd, cf, ghost, [&](int i, int xs, int ys) {
+        return Store<T>::load(src[(long long)i * gd.pitch + (long long)ys * gd.nx + xs]);
+    }, x, y);
+}
+
+// The border cells of an open 2D grid for one step of the learned edge, from the step's source
+// state and the network's entering populations (ghost[4][L]): one thread per border cell (corners
+// belong to the x-edges).  The interior cells come from the step kernel, which leaves these cells
+// unwritten (OpenEdge::skip_border), so the two can run at the same time.
 template <class S, class T>
 __global__ void k_edge_fixup(const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
-                             CollideCoef<typename Store<T>::C> cf, OpenEdge<typename Store<T>::C> ob) {
-    static_assert(S::D == 2, "border fix-up of 2D grids");
+                             CollideCoef<typename Store<T>::C> cf, const typename Store<T>::C *__restrict__ ghost,
+                             int L) {
     using C = typename Store<T>::C;
-    const int nx = gd.nx, ny = gd.ny, L = ob.ghost_L;
+    const int nx = gd.nx, ny = gd.ny;
     const int nb = 2 * ny + 2 * (nx - 2);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
         int x, y;
@@ -145,26 +187,7 @@ __global__ void k_edge_fixup(const T *__restrict__ src, T *__restrict__ dst, Gri
             x = 1 + (r - 2 * ny - (nx - 2));
             y = ny - 1;
         }
-        C pull[S::Q][1], post[S::Q][1];
-        static_for<S::Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int cx = S::c(i, 0), cy = S::c(i, 1);
-            const int xs = x - cx, ys = y - cy;
-            C v = C(0);
-            if (ys < 0 || ys >= ny) {  // enters through the bottom (c_y = +1) or top edge
-                if (cx == 0 && ob.ghost) v = ob.ghost[(cy == 1 ? 2 : 3) * L + x];
-            } else if (xs < 0) {  // through the left edge
-                if (cy == 0 && ob.ghost) v = ob.ghost[0 * L + y];
-            } else if (xs >= nx) {  // through the right edge
-                if (cy == 0 && ob.ghost) v = ob.ghost[1 * L + y];
-            } else {
-                v = Store<T>::load(src[(long long)i * gd.pitch + (long long)ys * nx + xs]);
-            }
-            pull[i][0] = v;
-        });
-        collide_cell<S, 0>(pull, post, cf);
-#pragma unroll
-        for (int i = 0; i < S::Q; ++i) dst[(long long)i * gd.pitch + (long long)y * nx + x] = Store<T>::make(post[i][0]);
+        edge_fixup_cell<S, T>(src, dst, gd, cf, [&](int e, int k) -> C { return ghost[e * L + k]; }, x, y);
     }
 }
 

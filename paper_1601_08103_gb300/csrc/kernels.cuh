@@ -179,6 +179,7 @@ struct OpenEdge {
     C sponge_smax;
     const C *ghost;      // nullptr = zero-incoming; else [4][L] entering populations (2D)
     int ghost_L;
+    int skip_border;     // 2D: leave the border cells unwritten (the learned edge's kernels own them)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -507,6 +508,22 @@ __device__ __forceinline__ void stream_collide_chunk(const T *__restrict__ src, 
 
     if (active) {
         T *outp = dst + ((long long)z * gd.ny + y) * gd.nx + x0;
+        if constexpr (OPEN && S::D == 2) {
+            if (ob.skip_border) {
+                if (y == 0 || y == gd.ny - 1) return;
+                if (x0 == 0 || x0 + V >= gd.nx) {  // a chunk that holds x = 0 or x = nx - 1
+                    static_for<S::Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+#pragma unroll
+                        for (int k = 0; k < V; ++k) {
+                            if (x0 + k >= 1 && x0 + k <= gd.nx - 2)
+                                outp[(long long)i * gd.pitch + k] = Store<T>::make(post[i][k]);
+                        }
+                    });
+                    return;
+                }
+            }
+        }
         static_for<S::Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             store_vec<T, V>(outp + (long long)i * gd.pitch, post[i]);

@@ -586,10 +586,12 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.wait_flag = h->wait_dev;
     L.wait_ns = g_stage_wait_ns.load(std::memory_order_relaxed);
     L.t3_inject = g_inject_stage.load(std::memory_order_relaxed);
-    // One time step's launches on stream `st`.  Learned edge: the boundary network runs on a side
-    // stream while the step runs with zero-incoming edges on `st`; after the join the border
-    // cells are pulled again with the network's entering populations.  Interior cells never read
-    // the ghosts, so the state is that of a step run with the ghosts throughout.
+    // One time step's launches on stream `st`.  Learned edge: on a side stream the boundary network
+    // computes the entering populations and k_edge_fixup writes the border cells of the new state,
+    // pulled with them and collided; meanwhile the step runs on `st` over the interior cells only
+    // (it leaves the border cells unwritten), then `st` joins the side stream.  Both read the same
+    // source state and write disjoint cells, and interior cells never read the ghosts, so the state
+    // is that of a step run with the ghosts throughout.
     if (learned && !h->side) {
         LEE_CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
         LEE_CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "fork event");
@@ -605,13 +607,19 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         if (e == cudaSuccess)
             e = launch_mlp_boundary(h->mlp, h->cfg.storage, h->buf[from], h->pitch, (int)h->cfg.nx, (int)h->cfg.ny,
                                     h->ghost, h->ghost_L, h->side);
+        if (e == cudaSuccess) {
+            StepLaunch F = L;
+            F.stream = h->side;
+            e = h->ops->edge_fixup(F);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
         if (e != cudaSuccess) return e;
-        L.ghost = nullptr;  // the whole grid with zero-incoming edges
+        L.ghost = nullptr;  // the interior cells, which no ghost reaches
+        L.skip_border = 1;
         e = h->ops->step(L);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
+        L.skip_border = 0;
         L.ghost = h->ghost;
-        if (e == cudaSuccess) e = h->ops->edge_fixup(L);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
         return e;
     };
     int64_t left = n;

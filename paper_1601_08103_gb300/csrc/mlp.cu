@@ -409,17 +409,28 @@ __global__ void k_edge_inputs(const T *__restrict__ g, long long pitch, int NX, 
 // Warp 0 runs layer 3 over the four k-chunks in order and applies the passivity bound.  Every
 // tile sees the same operations in the same order as in mlp_forward_warp, so the result is the
 // same bit for bit.
-constexpr int kBoundaryWarps = 4;
+constexpr int kBoundaryWarps = 8;  // warp j owns hidden units 8j .. 8j+7 of both hidden layers
 
+// Read-only 32-bit load of two consecutive BF16 weights from global memory.
+__device__ __forceinline__ uint32_t ldg_w(const __nv_bfloat16 *p) {
+    return __ldg(reinterpret_cast<const unsigned int *>(p));
+}
+
+// The learned edge's network for one grid: the entering populations ghost[e * L + k] of edge e at
+// position k.  Block b takes border rows 16b .. 16b+15 (16 rows = the M of one mma tile).  Its
+// critical path is one chain per warp: the strip loads, layer 1 (one mma and 4 GELU per lane), a
+// barrier, layer 2 (four mma, 4 GELU), a barrier, layer 3 (warp 0).  The weight fragments come
+// straight from global memory (L1/L2-resident, shared by every block) and are loaded while the
+// strips load, so no staging copy or barrier precedes layer 1.
 template <class T>
-__global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG, const T *__restrict__ g, long long pitch,
-                                                                      int NX, int NY,
-                                                                      typename Store<T>::C *__restrict__ ghost, int L) {
+__global__ void __launch_bounds__(32 * kBoundaryWarps)
+    k_mlp_boundary(MlpDev W, const T *__restrict__ g, long long pitch, int NX, int NY,
+                   typename Store<T>::C *__restrict__ ghost, int L) {
     using C = typename Store<T>::C;
-    __shared__ __align__(16) unsigned char wsm[kStagedWeightBytes];
     __shared__ float tile[16][kMlpIn];
     __shared__ float sc[16];
-    __shared__ uint32_t afrag1[kBoundaryWarps][32][4], afrag2[kBoundaryWarps][32][4];
+    // A fragments of layers 2 and 3: k-chunk kk (hidden units 16kk .. 16kk+15) from warps 2kk, 2kk+1
+    __shared__ uint32_t afrag1[4][32][4], afrag2[4][32][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = 2 * (NX + NY);
     const int row0 = blockIdx.x * 16;
@@ -436,58 +447,48 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG,
         for (int k = 0; k < kMlpIn; ++k) tile[threadIdx.x][k] = xv[k];
         sc[threadIdx.x] = s;
     }
-    const MlpDev W = stage_forward_weights(WG, wsm);  // ends with a block barrier
     const int gq = lane >> 2, t = lane & 3;
-    // layer 1, tiles 2w and 2w+1
+    const int j = warp;
+    const __nv_bfloat16 *w1p = W.w1 + (8 * j + gq) * kMlpIn + 2 * t;
+    const uint32_t w1a = ldg_w(w1p), w1b = ldg_w(w1p + 8);
+    uint32_t w2f[4][2];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const __nv_bfloat16 *w = W.w2 + (8 * j + gq) * kMlpHid + 16 * kk + 2 * t;
+        w2f[kk][0] = ldg_w(w);
+        w2f[kk][1] = ldg_w(w + 8);
+    }
+    const float b1a = __ldg(W.b1 + 8 * j + 2 * t), b1b = __ldg(W.b1 + 8 * j + 2 * t + 1);
+    const float b2a = __ldg(W.b2 + 8 * j + 2 * t), b2b = __ldg(W.b2 + 8 * j + 2 * t + 1);
+    __syncthreads();  // the strips are in the tile
+    // layer 1: tile j
     {
         uint32_t ax[4];
         a_frag_from_tile(tile, ax);
-        uint32_t h[2][2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int j = 2 * warp + q;
-            float z[4] = {0.f, 0.f, 0.f, 0.f};
-            const __nv_bfloat16 *w = W.w1 + (8 * j + gq) * kMlpIn + 2 * t;
-            mma16816(z, ax, ldw(w), ldw(w + 8));
-            const float bb0 = W.b1[8 * j + 2 * t], bb1 = W.b1[8 * j + 2 * t + 1];
-            z[0] += bb0;
-            z[1] += bb1;
-            z[2] += bb0;
-            z[3] += bb1;
-            h[q][0] = pack_bf16(gelu(z[0]), gelu(z[1]));
-            h[q][1] = pack_bf16(gelu(z[2]), gelu(z[3]));
-        }
-        afrag1[warp][lane][0] = h[0][0];
-        afrag1[warp][lane][1] = h[0][1];
-        afrag1[warp][lane][2] = h[1][0];
-        afrag1[warp][lane][3] = h[1][1];
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        mma16816(z, ax, w1a, w1b);
+        z[0] += b1a;
+        z[1] += b1b;
+        z[2] += b1a;
+        z[3] += b1b;
+        afrag1[j >> 1][lane][2 * (j & 1)] = pack_bf16(gelu(z[0]), gelu(z[1]));
+        afrag1[j >> 1][lane][2 * (j & 1) + 1] = pack_bf16(gelu(z[2]), gelu(z[3]));
     }
     __syncthreads();
-    // layer 2, tiles 2w and 2w+1, over the four k-chunks
+    // layer 2: tile j, over the four k-chunks
     {
-        uint32_t h[2][2];
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int j = 2 * warp + q;
-            float z[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t a[4] = {afrag1[kk][lane][0], afrag1[kk][lane][1], afrag1[kk][lane][2], afrag1[kk][lane][3]};
-                const __nv_bfloat16 *w = W.w2 + (8 * j + gq) * kMlpHid + 16 * kk + 2 * t;
-                mma16816(z, a, ldw(w), ldw(w + 8));
-            }
-            const float bb0 = W.b2[8 * j + 2 * t], bb1 = W.b2[8 * j + 2 * t + 1];
-            z[0] += bb0;
-            z[1] += bb1;
-            z[2] += bb0;
-            z[3] += bb1;
-            h[q][0] = pack_bf16(gelu(z[0]), gelu(z[1]));
-            h[q][1] = pack_bf16(gelu(z[2]), gelu(z[3]));
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t a[4] = {afrag1[kk][lane][0], afrag1[kk][lane][1], afrag1[kk][lane][2], afrag1[kk][lane][3]};
+            mma16816(z, a, w2f[kk][0], w2f[kk][1]);
         }
-        afrag2[warp][lane][0] = h[0][0];
-        afrag2[warp][lane][1] = h[0][1];
-        afrag2[warp][lane][2] = h[1][0];
-        afrag2[warp][lane][3] = h[1][1];
+        z[0] += b2a;
+        z[1] += b2b;
+        z[2] += b2a;
+        z[3] += b2b;
+        afrag2[j >> 1][lane][2 * (j & 1)] = pack_bf16(gelu(z[0]), gelu(z[1]));
+        afrag2[j >> 1][lane][2 * (j & 1) + 1] = pack_bf16(gelu(z[2]), gelu(z[3]));
     }
     __syncthreads();
     if (warp != 0) return;
@@ -496,9 +497,9 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps) k_mlp_boundary(MlpDev WG,
     for (int kk = 0; kk < 4; ++kk) {
         const uint32_t a[4] = {afrag2[kk][lane][0], afrag2[kk][lane][1], afrag2[kk][lane][2], afrag2[kk][lane][3]};
         const __nv_bfloat16 *w = W.w3 + gq * kMlpHid + 16 * kk + 2 * t;
-        mma16816(z3, a, ldw(w), ldw(w + 8));
+        mma16816(z3, a, ldg_w(w), ldg_w(w + 8));
     }
-    const float b3 = W.b3[0];
+    const float b3 = __ldg(W.b3);
     const float y_lo = z3[0] + b3, y_hi = z3[2] + b3;  // column 0 lives in lanes with t == 0
     // Passivity bound over the block's 16 border cells: the entering populations may carry at most
     // the weighted energy sum g^2 / f* of the outward populations leaving through the same cells
@@ -557,9 +558,20 @@ cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, 
     return with_store(storage, [&](auto *tp) {
         using T = std::remove_pointer_t<decltype(tp)>;
         using C = typename Store<T>::C;
-        k_mlp_boundary<T><<<blocks, 32 * kBoundaryWarps, 0, st>>>(W, static_cast<const T *>(g), pitch, NX, NY,
-                                                                  static_cast<C *>(ghost), L);
-        return cudaGetLastError();
+        // the network's blocks take the SMs before the step's (the network is the longer chain)
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return cudaGetLastError();
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3(blocks);
+        lc.blockDim = dim3(32 * kBoundaryWarps);
+        lc.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributePriority;
+        at[0].val.priority = hi;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        return cudaLaunchKernelEx(&lc, k_mlp_boundary<T>, W, static_cast<const T *>(g), pitch, NX, NY,
+                                  static_cast<C *>(ghost), L);
     });
 }
 

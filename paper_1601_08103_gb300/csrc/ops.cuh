@@ -33,6 +33,8 @@ struct StepLaunch {
     // for the TMA-fed kernel, where a timed-out stage wait is recorded (device-visible word, or
     // nullptr), the wait limit in ns (0: one second) and the test injection of such a timeout
     int t3_tma;
+    // open 2D grids: 1 = leave the border cells unwritten (the learned edge writes them)
+    int skip_border;
     unsigned *wait_flag;
     long long wait_ns;
     int t3_inject;
@@ -75,8 +77,8 @@ struct SetOps {
     // all steps of a small 1D grid in one launch, in place on g (nullptr for 2D/3D sets);
     // returns cudaErrorInvalidValue when the grid does not fit in shared memory
     cudaError_t (*onchip_1d)(const StepLaunch &L, void *g, long long nsteps);
-    // border cells of an open 2D grid pulled again with the entering populations L.ghost and
-    // collided (after a step with zero-incoming edges); nullptr for 1D/3D sets
+    // the border cells of an open 2D grid for one step of the learned edge (k_edge_fixup): pulled
+    // from L.src with the entering populations L.ghost, collided, stored in L.dst; nullptr for 1D/3D
     cudaError_t (*edge_fixup)(const StepLaunch &L);
     // slab halos: packs the populations that leave through the cut faces (first owned plane,
     // c_last = -1 -> send_lo; last owned plane, c_last = +1 -> send_hi), or unpacks the entering

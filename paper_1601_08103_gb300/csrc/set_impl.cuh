@@ -300,13 +300,13 @@ struct SetImpl {
                 if constexpr (std::is_same<T, Bfp16>::value) {
                     return cudaErrorInvalidValue;  // no learned edge on BFP16 storage
                 } else {
-                GridDesc gd{L.nx, L.ny, 1, L.nx, (long long)L.nx * L.ny, L.pitch};
-                const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
-                OpenEdge<C> ob{0, C(0), static_cast<const C *>(L.ghost), L.ghost_L};
-                const int nb = 2 * L.ny + 2 * (L.nx - 2);
-                k_edge_fixup<S, T><<<(nb + 127) / 128, 128, 0, L.stream>>>(static_cast<const T *>(L.src),
-                                                                          static_cast<T *>(L.dst), gd, cf, ob);
-                return cudaGetLastError();
+                    const GridDesc gd{L.nx, L.ny, 1, L.nx, (long long)L.nx * L.ny, L.pitch};
+                    const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
+                    const int nb = 2 * L.ny + 2 * (L.nx - 2);
+                    k_edge_fixup<S, T><<<(nb + 127) / 128, 128, 0, L.stream>>>(
+                        static_cast<const T *>(L.src), static_cast<T *>(L.dst), gd, cf, static_cast<const C *>(L.ghost),
+                        L.ghost_L);
+                    return cudaGetLastError();
                 }
             });
         }
@@ -326,7 +326,6 @@ struct SetImpl {
         o.slab_pack = S::D >= 2 ? &slab_pack : nullptr;
         o.slab_unpack = S::D >= 2 ? &slab_unpack : nullptr;
         o.slab_crossing = slab_crossing<S>();
-        o.edge_fixup = S::D == 2 ? &edge_fixup : nullptr;
         o.onchip_1d = S::D == 1 ? &onchip_1d : nullptr;
         o.step2 = S::D == 2 ? &step2 : nullptr;
         o.step2_prepare = S::D == 2 ? &step2_prepare : nullptr;
@@ -334,6 +333,7 @@ struct SetImpl {
         o.stepk_prepare = S::D == 2 ? &stepk_prepare : nullptr;
         o.step3d2 = axis_only<S>() ? &step3d2 : nullptr;
         o.step3d2_prepare = axis_only<S>() ? &step3d2_prepare : nullptr;
+        o.edge_fixup = S::D == 2 ? &edge_fixup : nullptr;
         for (int i = 0; i < S::Q; ++i) {
             for (int a = 0; a < 3; ++a) o.c[i][a] = S::c(i, a);
             o.shell[i] = S::shell(i);

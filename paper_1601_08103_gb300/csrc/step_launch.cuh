@@ -24,6 +24,7 @@ cudaError_t launch_step_v(const StepLaunch &L) {
     ob.sponge_smax = (C)L.sponge_smax;
     ob.ghost = static_cast<const C *>(L.ghost);
     ob.ghost_L = L.ghost_L;
+    ob.skip_border = L.skip_border;
     const long long blocks = (gd.nchunks + 255) / 256;
     k_stream_collide<S, T, V, OPEN, CUT><<<(unsigned)blocks, 256, 0, L.stream>>>(static_cast<const T *>(L.src),
                                                                                    static_cast<T *>(L.dst), gd, cf, ob);
