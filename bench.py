@@ -380,8 +380,22 @@ def forms_3d():
     out = {}
     ref = None
     stream = torch.cuda.current_stream()
-    for storage in ("f64", "f32", "f16", "bf16", "bfp16"):
-        with lee.Solver("D3Q7", (n, n, n), 0.55, storage=storage, stream=stream) as sv:
+    # (label, storage, environment at create time): the default kernels, and the TMA-fed two-step
+    # tile that LEE_T3_TMA=1 selects (measured slower; reported for the record)
+    forms = [(st, st, {}) for st in ("f64", "f32", "f16", "bf16", "bfp16")]
+    forms += [("f32_tma_tile", "f32", {"LEE_T3_TMA": "1"}), ("bfp16_tma_tile", "bfp16", {"LEE_T3_TMA": "1"})]
+    for label, storage, env in forms:
+        saved = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
+        try:
+            sv = lee.Solver("D3Q7", (n, n, n), 0.55, storage=storage, stream=stream)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        with sv:
             sv.init_fields(rho_d, u_d, th_d)
             sv.step(2)
             sv.init_fields(rho_d, u_d, th_d)
@@ -395,15 +409,15 @@ def forms_3d():
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             spl = sv.steps_per_launch
-        if storage == "f64":
+        if label == "f64":
             ref = r
         err = float(torch.linalg.norm(r - ref) / torch.linalg.norm(ref))
         bpl = 2 * 7 * lee.STORAGE_BYTES[storage]
-        out[storage] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
+        out[label] = {"mlups": round(cells * steps / (ms / 1e3) / 1e6, 1),
                         "gbs": round(bpl * cells * steps / (ms / 1e3) / 1e9, 1), "rel_l2_rho_vs_f64": err,
                         "steps_per_launch": spl, "bytes_per_update": round(bpl / max(spl, 1), 3)}
-    for storage in ("f16", "bf16", "bfp16"):
-        out[storage]["mlups_gain_vs_f32"] = round(out[storage]["mlups"] / out["f32"]["mlups"], 3)
+    for label in ("f16", "bf16", "bfp16", "f32_tma_tile", "bfp16_tma_tile"):
+        out[label]["mlups_gain_vs_f32"] = round(out[label]["mlups"] / out["f32"]["mlups"], 3)
     return {"workload": "3D D3Q7 periodic 384^3, tau=0.55, pulse A=1e-3 w=16, 500 steps", "storage": out,
             "error_reference": "the FP64 run on the GPU, which the tests hold to the oracle within 1e-12 "
                                "(test_full_size_3d_config_against_oracle also checks every storage against "
