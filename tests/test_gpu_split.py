@@ -100,11 +100,14 @@ def test_split_checkpoint_round_trip(gpu_lib):
 
 
 @pytest.mark.parametrize("name,shape", [("D3Q19", (128, 9, 6)), ("D3Q13", (128, 6, 5)), ("D2Q5", (256, 10, 1)),
-                                        ("D1Q3", (1024, 1, 1))])
+                                        ("D1Q3", (1024, 1, 1)), ("D3Q19", (64, 2, 3)), ("D3Q19", (192, 5, 1)),
+                                        ("D3Q19", (64, 3, 2)), ("D3Q7", (256, 7, 4)), ("D3Q9", (128, 4, 3)),
+                                        ("D3Q19", (64, 13, 11))])
 def test_split_tiled_vector_and_scalar_paths_agree_bitwise(gpu_lib, monkeypatch, name, shape):
     """Grids whose width is a multiple of 32 V run the y-tiled vector kernel (the last tile row
-    partly empty here); it computes every cell with the same arithmetic as the one-cell-per-thread
-    kernel, so the states agree bit for bit, and both match the oracle."""
+    partly empty, and grids of 1-3 rows or planes whose source rows wrap onto themselves, here);
+    it computes every cell with the same arithmetic as the one-cell-per-thread kernel, so the
+    states agree bit for bit, and both match the oracle."""
     lee = gpu_lib
     s = oracle.velset(name)
     cells = int(np.prod(shape))
