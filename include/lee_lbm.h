@@ -200,6 +200,9 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  *    encoding, bit for bit (LEE_TB_STEPS=1 or 2 keeps one step per launch, which equals decode,
  *    one FP32 step, encode).  On 3D grids BFP16 runs one step per launch unless LEE_TB_STEPS=2
  *    asks for the two-step tile (nx a multiple of 8), which is slower there;
+ *  - FP16 and BF16 storage on periodic 2D grids with nx a multiple of 4 do the same: four (or
+ *    three) steps per launch with the intermediate states in FP32, one rounding to the storage per
+ *    launch (LEE_TB_STEPS=1 or 2 keeps one step per launch, rounding every step);
  *  - a 1D grid (not BFP16) whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
@@ -289,9 +292,9 @@ lee_status lee_lbm_steps_done(lee_lbm *h, int64_t *steps);
  * intermediate states kept in shared memory -- temporal blocking; 4 unless LEE_TB_STEPS was set
  * at create time; periodic 3D FP32 D3Q7 and diatomic D3Q7 grids with nx a multiple of 4: 2;
  * BFP16 storage: 3 or 4 in 2D on such grids with nx a multiple of 8, 2 in 3D only with
- * LEE_TB_STEPS=2) or 0 (small 1D
+ * LEE_TB_STEPS=2; FP16 / BF16 storage: 3 or 4 in 2D on such grids) or 0 (small 1D
  * grid: all steps of a call in one on-chip launch).  All forms give bit-identical results, except
- * that BFP16 rounds its state once per launch (see lee_lbm_step). */
+ * that BFP16, FP16 and BF16 storage round their state once per launch (see lee_lbm_step). */
 lee_status lee_lbm_steps_per_launch(lee_lbm *h, int32_t *steps);
 
 /* The 16-bit storage scale S in use (1 for F64/F32/BFP16 storage). */

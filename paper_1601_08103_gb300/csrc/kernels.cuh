@@ -890,6 +890,41 @@ struct TileIoF32 {
     }
 };
 
+// FP16 / BF16 storage (S g / f*; the storage scale is folded into the collision coefficients, as
+// in the one-step kernel): 8-byte loads of a lane's four values, widened to FP32.  The levels in
+// between stay FP32 (the storage's 11 or 8 significant bits would otherwise be lost at every
+// level); S(t+K) is rounded to the storage once per launch, to nearest even like a one-step store.
+template <class T>
+struct TileIo16 {
+    using Elem = T;
+    using Vec = uint2;
+    using One = unsigned short;
+    __device__ static __forceinline__ float widen(unsigned bits) {
+        if constexpr (std::is_same<T, __half>::value) {
+            return __half2float(__ushort_as_half((unsigned short)bits));
+        } else {
+            return __bfloat162float(__ushort_as_bfloat16((unsigned short)bits));
+        }
+    }
+    __device__ static __forceinline__ Vec ld4(const T *__restrict__ base, long long, long long idx) {
+        return __ldg(reinterpret_cast<const uint2 *>(base + idx));
+    }
+    __device__ static __forceinline__ One ld1(const T *__restrict__ base, long long, long long idx) {
+        return __ldg(reinterpret_cast<const unsigned short *>(base + idx));
+    }
+    __device__ static __forceinline__ void cvt4(const Vec &t, float (&v)[4]) {
+        v[0] = widen(t.x & 0xFFFFu);  // element idx sits in the low half
+        v[1] = widen(t.x >> 16);
+        v[2] = widen(t.y & 0xFFFFu);
+        v[3] = widen(t.y >> 16);
+    }
+    __device__ static __forceinline__ float cvt1(const One &t) { return widen(t); }
+    __device__ static __forceinline__ void st4(T *__restrict__ base, long long, long long idx, const float (&v)[4],
+                                               bool store) {
+        if (store) store_vec<T, 4>(base + idx, v);
+    }
+};
+
 template <class S, int K, class IO>
 __device__ __forceinline__ void tbk_tile(const typename IO::Elem *__restrict__ src, typename IO::Elem *__restrict__ dst,
                                          int nx, int ny, long long pitch, int H, const CollideCoef<float> &cf, int x0,

@@ -148,13 +148,13 @@ lee_status fail(lee_lbm *h, lee_status s, const std::string &msg) {
 
 // Time steps fused per launch (temporal blocking): tb_steps on periodic 2D FP32 grids whose width
 // is a multiple of 4; two on periodic 3D FP32 grids of the axis-velocity sets whose width is a
-// multiple of 4; one step otherwise (16-bit storage moves half the bytes and stays on the one-step
-// kernel, which measured faster there).
+// multiple of 4; one step otherwise (in 3D, FP16/BF16 storage moves half the bytes and stays on the
+// one-step kernel, which measured faster there).
 //
-// BFP16 storage takes the same multi-step kernels (widths a multiple of its 8-cell block), with the
-// intermediate states in FP32 rather than rounded to the storage: a launch of k steps rounds once,
-// so its results depend on k (deterministically) and stay within the storage error of single
-// steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.  In 3D its
+// BFP16 storage (widths a multiple of its 8-cell block) and FP16/BF16 storage on periodic 2D grids
+// take the same K-step kernel, with the intermediate states in FP32 rather than rounded to the
+// storage: a launch of k steps rounds once, so its results depend on k (deterministically) and stay
+// within the storage error of single steps.  It has no two-step 2D kernel: LEE_TB_STEPS=2 keeps it on one step per launch.  In 3D its
 // two-step tile is taken only when LEE_TB_STEPS=2 asks for it: the decoding and encoding make that
 // latency-bound tile slower than the one-step kernel (D3Q7 384^3: 124 against 196 GLUPS).
 //
@@ -181,6 +181,10 @@ int fused_steps(const lee_lbm *h) {
     if (tiled_3d(h)) return 2;
     if (h->cfg.storage == LEE_STORE_BFP16) {
         const bool tiled = h->ops->stepk && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.nx % 8 == 0 && h->cfg.ny >= 3;
+        return tiled && h->tb_steps >= 3 ? h->tb_steps : 1;
+    }
+    if (h->cfg.storage == LEE_STORE_F16 || h->cfg.storage == LEE_STORE_BF16) {
+        const bool tiled = h->ops->stepk && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.nx % 4 == 0 && h->cfg.ny >= 3;
         return tiled && h->tb_steps >= 3 ? h->tb_steps : 1;
     }
     const bool tiled = h->ops->step2 && h->cfg.bc == LEE_BC_PERIODIC && h->cfg.storage == LEE_STORE_F32 &&
@@ -482,7 +486,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
         e = o->step2_prepare();
     if (e == cudaSuccess && o->stepk_prepare && h->tb_steps >= 3 && cfg->bc == LEE_BC_PERIODIC &&
-        (cfg->storage == LEE_STORE_F32 || cfg->storage == LEE_STORE_BFP16))
+        (cfg->storage == LEE_STORE_F32 || cfg->storage == LEE_STORE_BFP16 || cfg->storage == LEE_STORE_F16 ||
+         cfg->storage == LEE_STORE_BF16))
         e = o->stepk_prepare(h->tb_steps, cfg->storage);
     if (e == cudaSuccess && h->tb_steps >= 2 && tiled_3d(h)) e = o->step3d2_prepare(cfg->storage, tma_tile(h) ? 1 : 0);
     if (e == cudaSuccess && tma_tile(h)) {

@@ -247,19 +247,33 @@ struct SetImpl {
     }
     static cudaError_t step2_prepare() { return two_step_prepare<S>(); }
     static cudaError_t step2(const StepLaunch &L) { return two_step_launch<S>(L); }
-    // K = 3 or 4 steps per launch: FP32 storage (bit-identical to single steps) or BFP16 storage
-    // (FP32 levels in between, one encoding per launch)
+    // K = 3 or 4 steps per launch: FP32 storage (bit-identical to single steps), or BFP16, FP16 and
+    // BF16 storage (FP32 levels in between, one rounding to the storage per launch)
+    template <class IO>
+    static cudaError_t stepk_prepare_io(int k) {
+        return k == 3 ? kstep_prepare<S, 3, IO>() : k == 4 ? kstep_prepare<S, 4, IO>() : cudaErrorInvalidValue;
+    }
+    template <class IO>
+    static cudaError_t stepk_io(const StepLaunch &L, int k) {
+        return k == 3 ? kstep_launch<S, 3, IO>(L) : k == 4 ? kstep_launch<S, 4, IO>(L) : cudaErrorInvalidValue;
+    }
     static cudaError_t stepk_prepare(int k, int storage) {
-        using B = TileIoBfp<S::Q>;
-        if (storage == LEE_STORE_BFP16)
-            return k == 3 ? kstep_prepare<S, 3, B>() : k == 4 ? kstep_prepare<S, 4, B>() : cudaErrorInvalidValue;
-        return k == 3 ? kstep_prepare<S, 3>() : k == 4 ? kstep_prepare<S, 4>() : cudaErrorInvalidValue;
+        switch (storage) {
+        case LEE_STORE_BFP16: return stepk_prepare_io<TileIoBfp<S::Q>>(k);
+        case LEE_STORE_F16: return stepk_prepare_io<TileIo16<__half>>(k);
+        case LEE_STORE_BF16: return stepk_prepare_io<TileIo16<__nv_bfloat16>>(k);
+        case LEE_STORE_F32: return stepk_prepare_io<TileIoF32>(k);
+        default: return cudaErrorInvalidValue;
+        }
     }
     static cudaError_t stepk(const StepLaunch &L, int k) {
-        using B = TileIoBfp<S::Q>;
-        if (L.storage == LEE_STORE_BFP16)
-            return k == 3 ? kstep_launch<S, 3, B>(L) : k == 4 ? kstep_launch<S, 4, B>(L) : cudaErrorInvalidValue;
-        return k == 3 ? kstep_launch<S, 3>(L) : k == 4 ? kstep_launch<S, 4>(L) : cudaErrorInvalidValue;
+        switch (L.storage) {
+        case LEE_STORE_BFP16: return stepk_io<TileIoBfp<S::Q>>(L, k);
+        case LEE_STORE_F16: return stepk_io<TileIo16<__half>>(L, k);
+        case LEE_STORE_BF16: return stepk_io<TileIo16<__nv_bfloat16>>(L, k);
+        case LEE_STORE_F32: return stepk_io<TileIoF32>(L, k);
+        default: return cudaErrorInvalidValue;
+        }
     }
     // two steps per launch in 3D (axis-velocity sets; FP32 storage, or BFP16 with level 1 in FP32)
     // TMA-fed tile instantiations (one block per SM: the BFP16 tile needs 131 registers per thread

@@ -200,9 +200,12 @@ cudaError_t kstep_launch(const StepLaunch &L) {
     if constexpr (S::D != 2) {
         return cudaErrorInvalidValue;
     } else {
-        constexpr bool bfp = std::is_same<typename IO::Elem, Bfp16>::value;
-        if (L.storage != (bfp ? LEE_STORE_BFP16 : LEE_STORE_F32) || L.open || L.nx % (bfp ? kBfpBlock : 4) != 0 ||
-            L.ny < 3)
+        using E = typename IO::Elem;
+        constexpr bool bfp = std::is_same<E, Bfp16>::value;
+        constexpr int storage = bfp ? LEE_STORE_BFP16
+                                    : std::is_same<E, float>::value ? LEE_STORE_F32
+                                    : std::is_same<E, __half>::value ? LEE_STORE_F16 : LEE_STORE_BF16;
+        if (L.storage != storage || L.open || L.nx % (bfp ? kBfpBlock : 4) != 0 || L.ny < 3)
             return cudaErrorInvalidValue;
         const CollideCoef<float> cf = make_coef<float>(L.omega, L.coefM, L.coefN);
         constexpr int smem = tbk_smem_bytes<S, K>();
@@ -221,7 +224,6 @@ cudaError_t kstep_launch(const StepLaunch &L) {
         // No L2 prefetch: it helps the byte-bound two-step kernel on small grids, but this kernel
         // is bound by instruction issue, and the prefetch instructions cost more than they save
         // (measured on GB300, D2Q5 2048^2: 402 GLUPS without, 388 with).
-        using E = typename IO::Elem;
         k_stream_collide_kstep<S, K, IO><<<grid, kTbkThreads, smem, L.stream>>>(static_cast<const E *>(L.src),
                                                                          static_cast<E *>(L.dst), L.nx, L.ny, L.pitch,
                                                                          H, cf);

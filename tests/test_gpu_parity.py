@@ -415,7 +415,42 @@ def test_default_fuses_four_steps(gpu_lib, monkeypatch):
         assert sv.steps_per_launch == 4
     with lee.Solver("D2Q5", (2046, 64, 1), 0.6, storage="f32") as sv:  # nx not a multiple of 4
         assert sv.steps_per_launch == 1
-    with lee.Solver("D2Q5", (256, 64, 1), 0.6, storage="f16") as sv:
+    with lee.Solver("D2Q5", (256, 64, 1), 0.6, storage="f16") as sv:  # 16-bit: the same tile
+        assert sv.steps_per_launch == 4
+    with lee.Solver("D2Q5", (256, 64, 1), 0.6, storage="f16", bc="open_zero") as sv:
+        assert sv.steps_per_launch == 1
+
+
+@pytest.mark.parametrize("name", ["D2Q5", "D2Q5_DI"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_four_step_tile_rounds_once_per_launch(gpu_lib, monkeypatch, name, storage):
+    """Periodic 2D FP16 / BF16 grids with nx % 4 == 0 fuse four (or three) steps per launch and keep
+    the levels in between in FP32, so the state is rounded to the storage once per launch: on a
+    smooth pulse over 40 steps the result differs from one rounding per step, stays within the
+    storage bound and lands closer to the FP64 oracle (10 roundings against 40); a width that is
+    not a multiple of 4 keeps one step per launch."""
+    lee = gpu_lib
+    monkeypatch.delenv("LEE_SINGLE_STEP", raising=False)
+    s = oracle.velset(name)
+    unit = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    n = 40
+    for shape in ((256, 40, 1), (132, 37, 1)):
+        cells = int(np.prod(shape))
+        rho = inputs.gaussian_pulse(shape, 1e-3, 3.0, [m / 2.3 for m in shape])
+        u, th = inputs.zero_rest(s.D, cells)
+        errs, pops = {}, {}
+        for k in (1, 3, 4):
+            monkeypatch.setenv("LEE_TB_STEPS", str(k))
+            with lee.Solver(name, shape, 0.55, storage=storage) as sv:
+                assert sv.steps_per_launch == k
+            r = run_pair(lee, name, shape, 0.55, n, storage=storage, fields=(rho, u, th))
+            errs[k] = rel_l2(r["m_gpu"][0], r["m_ora"][0])
+            pops[k] = r["g_gpu"]
+            assert 0 < errs[k] <= 4 * unit * np.sqrt(10 * n), (shape, k, errs)
+        assert not np.array_equal(pops[1], pops[4])
+        assert errs[4] <= 0.85 * errs[1], (shape, errs)
+    monkeypatch.setenv("LEE_TB_STEPS", "4")
+    with lee.Solver(name, (130, 40, 1), 0.55, storage=storage) as sv:
         assert sv.steps_per_launch == 1
 
 
@@ -506,11 +541,11 @@ def test_3d_diatomic_pulse_in_dimensional_units(gpu_lib, storage):
 def test_vector_and_packed_paths_equal_the_scalar_path(gpu_lib, monkeypatch, name, storage, bc):
     """The vector kernels (several cells per thread; FP32 collisions on packed f32x2 pairs; the
     multi-step kernels) spell out every rounding like the one-cell-per-thread kernel, so a run gives
-    the same bits on both paths.  LEE_FORCE_SCALAR=1 at create time selects the scalar path.  BFP16
-    rounds once per launch, so its multi-step kernels are left out here (LEE_TB_STEPS=1); their
-    own test compares them with FP32 steps."""
+    the same bits on both paths.  LEE_FORCE_SCALAR=1 at create time selects the scalar path.  BFP16,
+    FP16 and BF16 round once per launch, so their multi-step kernels are left out here
+    (LEE_TB_STEPS=1); their own tests check them."""
     lee = gpu_lib
-    if storage == "bfp16":
+    if storage in ("bfp16", "f16", "bf16"):
         monkeypatch.setenv("LEE_TB_STEPS", "1")
     s = oracle.velset(name)
     shape = shapes_for(s.D, True)[0]
