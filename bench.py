@@ -808,6 +808,7 @@ CASES = {
     "d2q5_f32_4096": ("D2Q5", (4096, 4096, 1), "f32", 0.6),
     "d2q5_f32_8192": ("D2Q5", (8192, 8192, 1), "f32", 0.6),
     "d2q5_f16_8192": ("D2Q5", (8192, 8192, 1), "f16", 0.6),
+    "d2q5_f16_4096": ("D2Q5", (4096, 4096, 1), "f16", 0.6),
     "d2q5_bfp16_8192": ("D2Q5", (8192, 8192, 1), "bfp16", 0.6),
     "d2q5_bfp16": ("D2Q5", (2048, 2048, 1), "bfp16", 0.6),
     "d2q5_bfp16_4096": ("D2Q5", (4096, 4096, 1), "bfp16", 0.6),
