@@ -43,7 +43,11 @@ struct lee_lbm {
     // the stream they are captured on
     std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
     cudaStream_t cap = nullptr;
-    // learned edge: the network runs on `side` while the step runs on the handle's stream
+    // learned edge: the arrival counters of the four corner cells in the one-launch step
+    // (k_learned_step); with LEE_LEARNED_STREAMS=1 at create time the step runs as the network
+    // and the border cells on `side` while the interior runs on the handle's stream instead
+    unsigned *corner = nullptr;
+    bool learned_streams = false;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // time steps fused per launch on periodic 2D FP32 grids (temporal blocking): 4 by default;

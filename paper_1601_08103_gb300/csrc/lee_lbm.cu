@@ -20,6 +20,7 @@
 namespace lee {
 cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, long long pitch, int NX, int NY, void *ghost,
                                 int L, cudaStream_t st);
+cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned *corner);
 cudaError_t mlp_pack(const float *params_dev, void *packed, cudaStream_t st);
 extern const SetOps kOpsD1Q3, kOpsD2Q5, kOpsD2Q5Di, kOpsD3Q7, kOpsD3Q7Di, kOpsD3Q9, kOpsD3Q13, kOpsD3Q19;
 
@@ -267,6 +268,7 @@ void free_all(lee_lbm *h) {
     cudaFree(h->red_out);
     cudaFree(h->maxbits);
     cudaFree(h->ghost);
+    cudaFree(h->corner);
     cudaFree(h->mlp);
     for (void *p : h->halo) cudaFree(p);
     if (h->wait_host) cudaFreeHost(h->wait_host);
@@ -467,6 +469,7 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (const char *ev = std::getenv("LEE_T3_TMA")) {
         if ((ev[0] == '0' || ev[0] == '1') && ev[1] == 0) h->t3_tma = ev[0] - '0';
     }
+    if (const char *ev = std::getenv("LEE_LEARNED_STREAMS")) h->learned_streams = ev[0] == '1';
     if (h->force_scalar) h->tb_steps = 1;
     h->scale = scaled_storage(cfg->storage) ? (cfg->store_scale > 0.0 ? cfg->store_scale : 1.0) : 1.0;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -482,6 +485,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && cfg->bc == LEE_BC_OPEN_LEARNED) {
         h->ghost_L = (int)(cfg->nx > cfg->ny ? cfg->nx : cfg->ny);
         e = cudaMalloc(&h->ghost, (cfg->storage == LEE_STORE_F64 ? 8 : 4) * 4 * (size_t)h->ghost_L);
+        if (e == cudaSuccess) e = cudaMalloc(&h->corner, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->corner, 0, 4 * sizeof(unsigned), h->st);
     }
     if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
         e = o->step2_prepare();
@@ -591,13 +596,15 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
     L.wait_flag = h->wait_dev;
     L.wait_ns = g_stage_wait_ns.load(std::memory_order_relaxed);
     L.t3_inject = g_inject_stage.load(std::memory_order_relaxed);
-    // One time step's launches on stream `st`.  Learned edge: on a side stream the boundary network
-    // computes the entering populations and k_edge_fixup writes the border cells of the new state,
-    // pulled with them and collided; meanwhile the step runs on `st` over the interior cells only
-    // (it leaves the border cells unwritten), then `st` joins the side stream.  Both read the same
-    // source state and write disjoint cells, and interior cells never read the ghosts, so the state
-    // is that of a step run with the ghosts throughout.
-    if (learned && !h->side) {
+    // One time step's launches on stream `st`.  Learned edge: one launch of k_learned_step, whose
+    // first blocks run the boundary network and write the border cells of the new state (pulled
+    // with the entering populations and collided) while the others step the interior cells.  With
+    // LEE_LEARNED_STREAMS=1 the same work runs as three launches instead: on a side stream the
+    // network and k_edge_fixup (the border cells), meanwhile the step over the interior cells only
+    // on `st` (it leaves the border cells unwritten), then `st` joins the side stream.  Either way
+    // both parts read the same source state and write disjoint cells, and interior cells never
+    // read the entering populations, so the state is that of a step run with them throughout.
+    if (learned && h->learned_streams && !h->side) {
         LEE_CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
         LEE_CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "fork event");
         LEE_CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "join event");
@@ -607,6 +614,7 @@ lee_status lee_lbm_step(lee_lbm *h, int64_t n) {
         L.dst = state(h, from ^ 1);
         L.stream = st;
         if (!learned) return h->ops->step(L);
+        if (!h->learned_streams) return launch_learned_step(h->mlp, h->cfg.set, L, h->corner);
         cudaError_t e = cudaEventRecord(h->ev_fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
         if (e == cudaSuccess)

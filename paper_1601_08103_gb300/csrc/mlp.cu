@@ -12,6 +12,7 @@
 #include "../../include/lee_mlp.h"
 #include "handles.cuh"
 #include "mlp.cuh"
+#include "step_launch.cuh"
 
 namespace lee {
 
@@ -316,8 +317,24 @@ __global__ void k_mlp_adam(float *__restrict__ p, float *__restrict__ m, float *
 // ---------------------------------------------------------------------------------------------
 // edge strips of D2Q5 population fields (library order 0 rest, 1 +x, 2 -x, 3 +y, 4 -y)
 // ---------------------------------------------------------------------------------------------
-__constant__ int c_canon[4][5] = {{0, 1, 2, 3, 4}, {0, 2, 1, 4, 3}, {0, 3, 4, 2, 1}, {0, 4, 3, 1, 2}};
-__constant__ int c_normal[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+// Canonical slots of edge e: rest, the velocity along the inward normal (entering), the opposite one
+// (leaving), then the two tangential ones; canon(e, j) is the library velocity in slot j: edge 0
+// {0,1,2,3,4}, edge 1 {0,2,1,4,3}, edge 2 {0,3,4,2,1}, edge 3 {0,4,3,1,2}.  Packed 3 bits per slot
+// in a 16-bit field per edge, two edges per word, so that the lookup is register arithmetic.
+constexpr unsigned canon_word(int a, int b, int c, int d, int e) {
+    return (unsigned)(a | b << 3 | c << 6 | d << 9 | e << 12);
+}
+constexpr unsigned kCanon01 = canon_word(0, 1, 2, 3, 4) | canon_word(0, 2, 1, 4, 3) << 16;
+constexpr unsigned kCanon23 = canon_word(0, 3, 4, 2, 1) | canon_word(0, 4, 3, 1, 2) << 16;
+__host__ __device__ constexpr int canon(int e, int j) {
+    return (int)(((e < 2 ? kCanon01 : kCanon23) >> (16 * (e & 1) + 3 * j)) & 7u);
+}
+// Inward normal of edge e: (1, 0), (-1, 0), (0, 1), (0, -1).
+__host__ __device__ constexpr int normal_x(int e) { return (e == 0) - (e == 1); }
+__host__ __device__ constexpr int normal_y(int e) { return (e == 2) - (e == 3); }
+static_assert(canon(0, 4) == 4 && canon(1, 1) == 2 && canon(1, 3) == 4 && canon(2, 1) == 3 && canon(2, 4) == 1 &&
+                  canon(3, 1) == 4 && canon(3, 2) == 3 && canon(3, 4) == 2,
+              "canonical edge orders");
 
 struct EdgeRow {
     int e, k, cx, cy;
@@ -335,29 +352,40 @@ __device__ __forceinline__ EdgeRow edge_row(int r, int x0, int y0, int nx, int n
 
 // 1 / f* of D2Q5 (f* = 1/2 rest, 1/8 moving), exact.
 __device__ __forceinline__ float inv_f(int i) { return i == 0 ? 2.f : 8.f; }
+// f* itself; x / inv_f(i) == x * f_star(i) exactly (both are powers of two).
+__device__ __forceinline__ float f_star(int i) { return i == 0 ? 0.5f : 0.125f; }
 
-// Strip inputs x[16] and scale s of one border row.
+// Value k of the strip of border row E (depth d = k / 5 from the edge, canonical slot k % 5), in
+// units of f* (x 1/f* for unscaled storage).
 template <class T>
-__device__ __forceinline__ void strip_inputs(const T *__restrict__ g, long long pitch, int NX, const EdgeRow &E, bool scaled,
-                                             float (&xv)[kMlpIn], float &s) {
+__device__ __forceinline__ float strip_value(const T *__restrict__ g, long long pitch, int NX, const EdgeRow &E,
+                                             bool scaled, int k) {
+    const int d = k / 5, i = canon(E.e, k - 5 * d);
+    const int px = E.cx + d * normal_x(E.e), py = E.cy + d * normal_y(E.e);
+    float h = (float)Store<T>::load(g[(long long)i * pitch + px + (long long)NX * py]);
+    if (!scaled) h *= inv_f(i);
+    return h;
+}
+// Scale of a strip from its 15 values xv[0..14] (slot k = 5 d + j: depth d, canonical slot j), and
+// the values divided by it, in place (registers or shared memory); xv[15] = 0 pads the row to the
+// mma's K.
+__device__ __forceinline__ void strip_finish(float *xv, float &s) {
     float ss = 0.f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int px = E.cx + d * c_normal[E.e][0], py = E.cy + d * c_normal[E.e][1];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            const int i = c_canon[E.e][j];
-            float h = (float)Store<T>::load(g[(long long)i * pitch + px + (long long)NX * py]);
-            if (!scaled) h *= inv_f(i);
-            xv[5 * d + j] = h;
-            ss += h * h;
-        }
-    }
+    for (int k = 0; k < 15; ++k) ss += xv[k] * xv[k];
     s = fmaxf(sqrtf(ss / 15.f), 1e-30f);
     const float inv = 1.f / s;
 #pragma unroll
     for (int k = 0; k < 15; ++k) xv[k] *= inv;
     xv[15] = 0.f;
+}
+// Strip inputs x[16] and scale s of one border row.
+template <class T>
+__device__ __forceinline__ void strip_inputs(const T *__restrict__ g, long long pitch, int NX, const EdgeRow &E, bool scaled,
+                                             float (&xv)[kMlpIn], float &s) {
+#pragma unroll
+    for (int k = 0; k < 15; ++k) xv[k] = strip_value<T>(g, pitch, NX, E, scaled, k);
+    strip_finish(xv, s);
 }
 
 // Training pairs from a batch: one thread per border row of one domain.
@@ -375,8 +403,8 @@ __global__ void k_edge_samples(const T *__restrict__ buf, const long long *__res
     strip_inputs<T>(g, pitch[d], dnx[d], E, Store<T>::scaled, xv, s);
 #pragma unroll
     for (int k = 0; k < kMlpIn; ++k) xo[row * kMlpIn + k] = xv[k];
-    const int iin = c_canon[E.e][1];
-    const int ox = E.cx - c_normal[E.e][0], oy = E.cy - c_normal[E.e][1];
+    const int iin = canon(E.e, 1);
+    const int ox = E.cx - normal_x(E.e), oy = E.cy - normal_y(E.e);
     float tv = (float)Store<T>::load(g[(long long)iin * pitch[d] + ox + (long long)dnx[d] * oy]);
     if (!Store<T>::scaled) tv *= inv_f(iin);
     to[row] = tv / s;
@@ -401,14 +429,14 @@ __global__ void k_edge_inputs(const T *__restrict__ g, long long pitch, int NX, 
 // The learned boundary of one step: strips of the current post-collision state -> network ->
 // entering populations ghost[4][L] (arithmetic type C of the storage).
 //
-// One block of 4 warps per group of 16 border rows.  The chain of three dependent layers is what
-// bounds this kernel, so the hidden units are split over the warps: warp w computes hidden units
-// 16 w .. 16 w + 15 of layers 1 and 2 (two 8-column tiles each).  The C fragments of a warp's two
-// tiles are exactly the A fragment of k-chunk w of the next layer, and that per-lane layout is the
-// same in every warp, so the fragments pass between warps through shared memory as they are.
-// Warp 0 runs layer 3 over the four k-chunks in order and applies the passivity bound.  Every
-// tile sees the same operations in the same order as in mlp_forward_warp, so the result is the
-// same bit for bit.
+// One block of 8 warps per group of 16 border rows.  The chain of three dependent layers is what
+// bounds this work, so the hidden units are split over the warps: warp j computes hidden units
+// 8j .. 8j+7 of layers 1 and 2 (one 8-column tile each).  The C fragment of a warp's tile is half
+// of the A fragment of k-chunk j/2 of the next layer, and that per-lane layout is the same in
+// every warp, so the fragments pass between warps through shared memory as they are.  Warp 0
+// runs layer 3 over the four k-chunks in order and applies the passivity bound.  Every tile sees
+// the same operations in the same order as in mlp_forward_warp, so the result is the same bit for
+// bit.
 constexpr int kBoundaryWarps = 8;  // warp j owns hidden units 8j .. 8j+7 of both hidden layers
 
 // Read-only 32-bit load of two consecutive BF16 weights from global memory.
@@ -416,36 +444,31 @@ __device__ __forceinline__ uint32_t ldg_w(const __nv_bfloat16 *p) {
     return __ldg(reinterpret_cast<const unsigned int *>(p));
 }
 
-// The learned edge's network for one grid: the entering populations ghost[e * L + k] of edge e at
-// position k.  Block b takes border rows 16b .. 16b+15 (16 rows = the M of one mma tile).  Its
-// critical path is one chain per warp: the strip loads, layer 1 (one mma and 4 GELU per lane), a
-// barrier, layer 2 (four mma, 4 GELU), a barrier, layer 3 (warp 0).  The weight fragments come
-// straight from global memory (L1/L2-resident, shared by every block) and are loaded while the
-// strips load, so no staging copy or barrier precedes layer 1.
+// The network over border rows row0 .. row0+15 of one grid; every thread of the block calls it.
+// The critical path is one chain per warp: the strip loads (one value per thread: row tid / 16,
+// slot tid % 16), a barrier, the strip scales (one thread per row), a barrier, layer 1 (one mma
+// and 4 GELU per lane), a barrier, layer 2 (four mma, 4 GELU), a barrier, layer 3 (warp 0).  The
+// weight fragments come straight from global memory (L1/L2-resident, shared by every block) and
+// are loaded while the strips load, so no staging copy precedes layer 1.
+// Returns false in warps 1..7 once layer 2 is done; in warp 0 it returns true, and each lane
+// with t = lane % 4 == 0 holds in v[h] the entering population of row row0 + lane/4 + 8h in
+// stored units (network output x strip scale x passivity factor, times f* for unscaled storage),
+// still in FP32; rows at or beyond 2 (NX + NY) hold 0.
 template <class T>
-__global__ void __launch_bounds__(32 * kBoundaryWarps)
-    k_mlp_boundary(MlpDev W, const T *__restrict__ g, long long pitch, int NX, int NY,
-                   typename Store<T>::C *__restrict__ ghost, int L) {
-    using C = typename Store<T>::C;
+__device__ __forceinline__ bool boundary_rows(const MlpDev &W, const T *__restrict__ g, long long pitch, int NX,
+                                              int NY, int row0, float (&v)[2]) {
+    static_assert(kBoundaryWarps * 32 == 16 * 16, "one thread per strip value of 16 rows");
     __shared__ float tile[16][kMlpIn];
     __shared__ float sc[16];
     // A fragments of layers 2 and 3: k-chunk kk (hidden units 16kk .. 16kk+15) from warps 2kk, 2kk+1
     __shared__ uint32_t afrag1[4][32][4], afrag2[4][32][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = 2 * (NX + NY);
-    const int row0 = blockIdx.x * 16;
-    if (threadIdx.x < 16) {
-        const int r = row0 + threadIdx.x;
-        float xv[kMlpIn], s = 1.f;
-        if (r < R) {
-            strip_inputs<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, xv, s);
-        } else {
-#pragma unroll
-            for (int k = 0; k < kMlpIn; ++k) xv[k] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) tile[threadIdx.x][k] = xv[k];
-        sc[threadIdx.x] = s;
+    {
+        const int lr = threadIdx.x >> 4, k = threadIdx.x & 15, r = row0 + lr;
+        float h = 0.f;
+        if (k < 15 && r < R) h = strip_value<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, k);
+        tile[lr][k] = h;
     }
     const int gq = lane >> 2, t = lane & 3;
     const int j = warp;
@@ -460,7 +483,13 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps)
     }
     const float b1a = __ldg(W.b1 + 8 * j + 2 * t), b1b = __ldg(W.b1 + 8 * j + 2 * t + 1);
     const float b2a = __ldg(W.b2 + 8 * j + 2 * t), b2b = __ldg(W.b2 + 8 * j + 2 * t + 1);
-    __syncthreads();  // the strips are in the tile
+    __syncthreads();  // the raw strips are in the tile
+    if (threadIdx.x < 16) {
+        float s = 1.f;
+        if (row0 + (int)threadIdx.x < R) strip_finish(tile[threadIdx.x], s);  // rows past the border stay 0
+        sc[threadIdx.x] = s;
+    }
+    __syncthreads();  // the scaled strips are in the tile
     // layer 1: tile j
     {
         uint32_t ax[4];
@@ -491,7 +520,7 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps)
         afrag2[j >> 1][lane][2 * (j & 1) + 1] = pack_bf16(gelu(z[2]), gelu(z[3]));
     }
     __syncthreads();
-    if (warp != 0) return;
+    if (warp != 0) return false;
     float z3[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
@@ -521,19 +550,34 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps)
         ein += __shfl_xor_sync(0xffffffffu, ein, off);
         eout += __shfl_xor_sync(0xffffffffu, eout, off);
     }
-    const float factor = ein > eout ? sqrtf(eout / ein) : 1.f;
-    if (t == 0) {
+    float factor = 1.f;
+    if (ein > eout) factor = sqrtf(eout / ein);
+    // the entering velocity (canonical slot 1) moves, so f* = 1/8 for it
+    const float fs = Store<T>::scaled ? 1.f : f_star(canon(0, 1));
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int lr = gq + 8 * h;
-            const int r = row0 + lr;
-            if (r < R) {
-                const EdgeRow E = edge_row(r, 0, 0, NX, NY);
-                const int iin = c_canon[E.e][1];
-                float v = vin[h] * factor;
-                if (!Store<T>::scaled) v /= inv_f(iin);
-                ghost[E.e * L + E.k] = (C)v;
-            }
+    for (int h = 0; h < 2; ++h) v[h] = vin[h] * factor * fs;
+    return true;
+}
+
+// The learned edge's network for one grid: the entering populations ghost[e * L + k] of edge e at
+// position k.  Block b takes border rows 16b .. 16b+15 (16 rows = the M of one mma tile).
+template <class T>
+__global__ void __launch_bounds__(32 * kBoundaryWarps)
+    k_mlp_boundary(MlpDev W, const T *__restrict__ g, long long pitch, int NX, int NY,
+                   typename Store<T>::C *__restrict__ ghost, int L) {
+    using C = typename Store<T>::C;
+    const int row0 = blockIdx.x * 16;
+    float v[2];
+    if (!boundary_rows<T>(W, g, pitch, NX, NY, row0, v)) return;
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) != 0) return;
+    const int R = 2 * (NX + NY);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = row0 + (lane >> 2) + 8 * h;
+        if (r < R) {
+            const EdgeRow E = edge_row(r, 0, 0, NX, NY);
+            ghost[E.e * L + E.k] = (C)v[h];
         }
     }
 }
@@ -573,6 +617,149 @@ cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, 
         return cudaLaunchKernelEx(&lc, k_mlp_boundary<T>, W, static_cast<const T *>(g), pitch, NX, NY,
                                   static_cast<C *>(ghost), L);
     });
+}
+
+// ---------------------------------------------------------------------------------------------
+// one learned step in one launch
+// ---------------------------------------------------------------------------------------------
+
+// The in-grid pulls of border cell (x, y): pre[i] = the stored value of velocity i at (x - c_i),
+// 0 where that cell is outside the grid (an entering population, which the network supplies).
+template <class S, class T>
+__device__ __forceinline__ void border_pulls(const T *__restrict__ src, const GridDesc &gd, int x, int y,
+                                             typename Store<T>::C (&pre)[S::Q]) {
+    using C = typename Store<T>::C;
+    static_for<S::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const int xs = x - S::c(i, 0), ys = y - S::c(i, 1);
+        pre[i] = (xs >= 0 && xs < gd.nx && ys >= 0 && ys < gd.ny)
+                     ? Store<T>::load(src[(long long)i * gd.pitch + (long long)ys * gd.nx + xs])
+                     : C(0);
+    });
+}
+
+// A load served by L2 (not L1, which is not coherent with other SMs' stores within a launch).
+template <class C>
+__device__ __forceinline__ C load_l2(const C *p) {
+    static_assert(sizeof(C) == 8 || sizeof(C) == 4, "entering populations are FP64 or FP32");
+    if constexpr (sizeof(C) == 8) {
+        const unsigned long long b = __ldcg(reinterpret_cast<const unsigned long long *>(p));
+        return __longlong_as_double((long long)b);
+    } else {
+        return __uint_as_float(__ldcg(reinterpret_cast<const unsigned int *>(p)));
+    }
+}
+
+// Resident blocks per SM the fused kernel's registers are sized for: those of the one-step kernel
+// over the same cells (5 at 48 registers; 3 for the 16-bit vector forms, which need about 72).
+template <class T, int V>
+constexpr int learned_min_blocks() {
+    return sizeof(T) == 2 && V > 1 ? 3 : 5;
+}
+
+// One time step of an open 2D grid with the learned edge, in one launch (equal bit for bit to the
+// network kernel, k_edge_fixup and the step over the interior cells):
+//  - blocks 0 .. nnet-1 each run the network for 16 border rows (boundary_rows) and then write
+//    those rows' border cells.  Lanes 16..31 of warp 0 own the cells: they load the cells' in-grid
+//    pulls while the strips load, take the entering populations from lanes t == 0 by shuffle,
+//    store them into ghost[] and collide (k_edge_fixup's arithmetic);
+//  - a corner cell takes the entering populations of two rows, an x-edge one and a y-edge one,
+//    possibly in two blocks.  Each of the two lanes stores its value, fences and counts one
+//    arrival on the corner's counter; the lane whose arrival is the second of the step (an odd
+//    count before it: two arrivals per step, the counters start at 0) reads the other value from
+//    L2 and writes the corner.  Nothing waits;
+//  - the other blocks run the one-step stream-collide chunks over the interior cells, leaving the
+//    border unwritten (OpenEdge::skip_border).
+// The network blocks come first in the grid, so they are dispatched first and their dependent
+// chain overlaps the interior's memory traffic.
+template <class S, class T, int V>
+__global__ void __launch_bounds__(32 * kBoundaryWarps, learned_min_blocks<T, V>())
+    k_learned_step(MlpDev W, const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
+                   CollideCoef<typename Store<T>::C> cf, OpenEdge<typename Store<T>::C> ob,
+                   typename Store<T>::C *__restrict__ ghost, int L, unsigned *__restrict__ corner, int nnet) {
+    using C = typename Store<T>::C;
+    static_assert(32 * kBoundaryWarps == 256, "the interior chunks take 256 threads per block");
+    if ((int)blockIdx.x >= nnet) {
+        stream_collide_chunk<S, T, V, true>(src, dst, gd, cf, ob,
+                                            (long long)(blockIdx.x - nnet) * blockDim.x + threadIdx.x);
+        return;
+    }
+    const int NX = gd.nx, NY = gd.ny, R = 2 * (NX + NY);
+    const int row0 = blockIdx.x * 16;
+    const int lane = threadIdx.x & 31, lr = (lane - 16) & 15;  // lanes 16..31: row row0 + lr
+    const bool own = threadIdx.x >= 16 && threadIdx.x < 32 && row0 + lr < R;
+    EdgeRow F{0, 0, 0, 0};
+    C pre[S::Q];
+    if (own) {
+        F = edge_row(row0 + lr, 0, 0, NX, NY);
+        border_pulls<S, T>(src, gd, F.cx, F.cy, pre);
+    }
+    float v[2];
+    if (!boundary_rows<T>(W, src, gd.pitch, NX, NY, row0, v)) return;
+    // row lr's value sits in lane 4 (lr % 8), slot lr / 8
+    const float v0 = __shfl_sync(0xffffffffu, v[0], 4 * (lr & 7));
+    const float v1 = __shfl_sync(0xffffffffu, v[1], 4 * (lr & 7));
+    if (!own) return;
+    const C gv = (C)(lr < 8 ? v0 : v1);
+    ghost[F.e * L + F.k] = gv;
+    auto pulled = [&](int i, int, int) -> C { return pre[i]; };
+    const int kmax = (F.e < 2 ? NY : NX) - 1;
+    if (F.k != 0 && F.k != kmax) {
+        edge_fixup_cell_from<S, T>(dst, gd, cf, [&](int, int) -> C { return gv; }, pulled, F.cx, F.cy);
+        return;
+    }
+    __threadfence();
+    const unsigned before = atomicAdd(corner + (F.cx == 0 ? 0 : 1) + (F.cy == 0 ? 0 : 2), 1u);
+    if ((before & 1u) == 0u) return;  // the corner's other row completes it
+    __threadfence();
+    edge_fixup_cell_from<S, T>(
+        dst, gd, cf, [&](int e, int k) -> C { return e == F.e ? gv : load_l2(ghost + e * L + k); }, pulled, F.cx,
+        F.cy);
+}
+
+template <class S, class T, int V>
+cudaError_t launch_learned_v(const MlpDev &W, const StepLaunch &L, unsigned *corner) {
+    using C = typename Store<T>::C;
+    GridDesc gd;
+    gd.nx = L.nx;
+    gd.ny = L.ny;
+    gd.nz = 1;
+    gd.nxc = L.nx / V;
+    gd.nchunks = (long long)gd.nxc * L.ny;
+    gd.pitch = L.pitch;
+    const CollideCoef<C> cf = make_coef<C>(L.omega, L.coefM, L.coefN);
+    OpenEdge<C> ob;
+    ob.sponge_w = L.sponge_w;
+    ob.sponge_smax = (C)L.sponge_smax;
+    ob.ghost = nullptr;  // interior cells never read the entering populations
+    ob.ghost_L = 0;
+    ob.skip_border = 1;
+    const int nnet = (2 * (L.nx + L.ny) + 15) / 16;
+    const long long blocks = nnet + (gd.nchunks + 255) / 256;
+    k_learned_step<S, T, V><<<(unsigned)blocks, 32 * kBoundaryWarps, 0, L.stream>>>(
+        W, static_cast<const T *>(L.src), static_cast<T *>(L.dst), gd, cf, ob, static_cast<C *>(const_cast<void *>(L.ghost)),
+        L.ghost_L, corner, nnet);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t launch_learned_s(const MlpDev &W, const StepLaunch &L, unsigned *corner) {
+    return with_store(L.storage, [&](auto *tp) -> cudaError_t {
+        using T = std::remove_pointer_t<decltype(tp)>;
+        constexpr int V = vec_width<S, T>();
+        if (!L.force_scalar && L.nx % V == 0) return launch_learned_v<S, T, V>(W, L, corner);
+        return launch_learned_v<S, T, 1>(W, L, corner);
+    });
+}
+
+// Called by lee_lbm_step for LEE_BC_OPEN_LEARNED (D2Q5): the whole step
+// in one launch of k_learned_step, reading L.src and writing L.dst and the entering populations
+// L.ghost[4][L.ghost_L]; corner = 4 arrival counters (zero at create, even between launches).
+cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned *corner) {
+    if (!L.ghost || !corner || L.nx < 3 || L.ny < 3 || L.nz != 1) return cudaErrorInvalidValue;
+    const MlpDev W = mlp_dev(packed);
+    if (set != LEE_D2Q5) return cudaErrorInvalidValue;  // the network is trained on this set only
+    return launch_learned_s<D2Q5>(W, L, corner);
 }
 
 }  // namespace lee

@@ -220,3 +220,54 @@ def test_learned_boundary_step_matches_oracle(gpu_lib, storage):
     r_ora = oracle.moments("D2Q5", g)[0]
     err = np.linalg.norm(r_gpu - r_ora) / np.linalg.norm(r_ora)
     assert err < (1e-5 if storage == "f64" else 3e-5), err
+
+
+def _learned_run(lee, monkeypatch, env, name, shape, storage, params, fields, calls):
+    for k in ("LEE_LEARNED_STREAMS", "LEE_FORCE_SCALAR"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    q = lee.lee_velset_info(name)["q"]
+    with lee.Solver(name, shape, 0.6, storage=storage, bc="open_learned") as sv:
+        sv.set_boundary_mlp(params)
+        sv.init_fields(*fields)
+        for n in calls:
+            sv.step(n)
+        g = np.empty((q, int(np.prod(shape))))
+        sv.get_populations(g)
+    return g
+
+
+LEARNED_SHAPES = [(48, 33, 1), (64, 64, 1), (3, 3, 1), (5, 4, 1), (7, 130, 1), (130, 7, 1), (257, 19, 1)]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", LEARNED_SHAPES)
+def test_one_launch_learned_step_equals_three_launch_form(gpu_lib, monkeypatch, storage, shape):
+    """k_learned_step (network blocks that also write their border cells, corner cells completed by
+    the second of their two rows, interior blocks) against the network kernel + k_edge_fixup on a
+    side stream and the interior step (LEE_LEARNED_STREAMS=1): equal bit for bit, through a
+    captured graph (10 steps), direct launches (3, then 1) and another graph (8), so the corner
+    counters cross launches of both kinds.  Shapes cover grids with fewer than 16 border rows,
+    border rows not a multiple of 16, and widths that take the one-cell-per-thread interior."""
+    lee = gpu_lib
+    D = 2
+    params = (omlp.init_params(31) * 0.5).astype(np.float32)
+    fields = inputs.random_fields(shape, D, 41)
+    calls = (10, 3, 1, 8)
+    g1 = _learned_run(lee, monkeypatch, {}, "D2Q5", shape, storage, params, fields, calls)
+    g3 = _learned_run(lee, monkeypatch, {"LEE_LEARNED_STREAMS": "1"}, "D2Q5", shape, storage, params, fields, calls)
+    assert np.isfinite(g1).all()
+    assert np.array_equal(g1, g3)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_one_launch_learned_step_scalar_interior(gpu_lib, monkeypatch, storage):
+    """LEE_FORCE_SCALAR=1 (one cell per interior thread) gives the same state as the vector form."""
+    lee = gpu_lib
+    shape = (64, 40, 1)
+    params = (omlp.init_params(32) * 0.5).astype(np.float32)
+    fields = inputs.random_fields(shape, 2, 43)
+    g_v = _learned_run(lee, monkeypatch, {}, "D2Q5", shape, storage, params, fields, (9,))
+    g_s = _learned_run(lee, monkeypatch, {"LEE_FORCE_SCALAR": "1"}, "D2Q5", shape, storage, params, fields, (9,))
+    assert np.array_equal(g_v, g_s)
