@@ -206,9 +206,11 @@ lee_status lee_lbm_init_fields(lee_lbm *h, const double *rho, const double *u, c
  *  - a 1D grid (not BFP16) whose two population copies fit in shared memory (2 q nx sizeof(storage) <= 227 KB,
  *    e.g. D1Q3 FP64 up to 4843 cells) runs all n >= 2 steps in one launch: one block, or from
  *    512 cells a thread-block cluster of 8 blocks;
- *  - OPEN_LEARNED: the boundary network runs on a second stream while the step runs with
- *    zero-incoming edges; the border cells are then pulled again with the network's entering
- *    populations and collided (the stream waits for both before returning work to the caller). */
+ *  - OPEN_LEARNED: one launch per step whose first blocks run the boundary network and write the
+ *    border cells (pulled with the network's entering populations and collided) while the other
+ *    blocks step the interior cells; LEE_LEARNED_STREAMS=1 in the environment at create time runs
+ *    the same work as three launches instead (network and border cells on a second stream beside
+ *    the interior step, joined before the next step), with the same result bit for bit. */
 lee_status lee_lbm_step(lee_lbm *h, int64_t n);
 
 /* Per-cell moments of the current state (Sec. 4 discrete moments; Sec. 5 temperature for
