@@ -238,7 +238,8 @@ def _learned_run(lee, monkeypatch, env, name, shape, storage, params, fields, ca
     return g
 
 
-LEARNED_SHAPES = [(48, 33, 1), (64, 64, 1), (3, 3, 1), (5, 4, 1), (7, 130, 1), (130, 7, 1), (257, 19, 1)]
+LEARNED_SHAPES = [(48, 33, 1), (64, 64, 1), (3, 3, 1), (5, 4, 1), (7, 130, 1), (130, 7, 1), (257, 19, 1),
+                  (2048, 2048, 1), (4100, 12, 1)]
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
@@ -249,7 +250,8 @@ def test_one_launch_learned_step_equals_three_launch_form(gpu_lib, monkeypatch, 
     side stream and the interior step (LEE_LEARNED_STREAMS=1): equal bit for bit, through a
     captured graph (10 steps), direct launches (3, then 1) and another graph (8), so the corner
     counters cross launches of both kinds.  Shapes cover grids with fewer than 16 border rows,
-    border rows not a multiple of 16, and widths that take the one-cell-per-thread interior."""
+    border rows not a multiple of 16, widths that take the one-cell-per-thread interior, and a
+    2048^2 grid (1024 network blocks beside 4096 interior blocks)."""
     lee = gpu_lib
     D = 2
     params = (omlp.init_params(31) * 0.5).astype(np.float32)
