@@ -446,10 +446,10 @@ __device__ __forceinline__ uint32_t ldg_w(const __nv_bfloat16 *p) {
 
 // The network over border rows row0 .. row0+15 of one grid; every thread of the block calls it.
 // The critical path is one chain per warp: the strip loads (one value per thread: row tid / 16,
-// slot tid % 16), a barrier, the strip scales (one thread per row), a barrier, layer 1 (one mma
-// and 4 GELU per lane), a barrier, layer 2 (four mma, 4 GELU), a barrier, layer 3 (warp 0).  The
-// weight fragments come straight from global memory (L1/L2-resident, shared by every block) and
-// are loaded while the strips load, so no staging copy precedes layer 1.
+// slot tid % 16) and the strip scales (shuffles within the row's 16 lanes), a barrier, layer 1
+// (one mma and 4 GELU per lane), a barrier, layer 2 (four mma, 4 GELU), a barrier, layer 3
+// (warp 0).  The weight fragments come straight from global memory (L1/L2-resident, shared by
+// every block) and are loaded while the strips load, so no staging copy precedes layer 1.
 // Returns false in warps 1..7 once layer 2 is done; in warp 0 it returns true, and each lane
 // with t = lane % 4 == 0 holds in v[h] the entering population of row row0 + lane/4 + 8h in
 // stored units (network output x strip scale x passivity factor, times f* for unscaled storage),
@@ -464,12 +464,6 @@ __device__ __forceinline__ bool boundary_rows(const MlpDev &W, const T *__restri
     __shared__ uint32_t afrag1[4][32][4], afrag2[4][32][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int R = 2 * (NX + NY);
-    {
-        const int lr = threadIdx.x >> 4, k = threadIdx.x & 15, r = row0 + lr;
-        float h = 0.f;
-        if (k < 15 && r < R) h = strip_value<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, k);
-        tile[lr][k] = h;
-    }
     const int gq = lane >> 2, t = lane & 3;
     const int j = warp;
     const __nv_bfloat16 *w1p = W.w1 + (8 * j + gq) * kMlpIn + 2 * t;
@@ -483,11 +477,22 @@ __device__ __forceinline__ bool boundary_rows(const MlpDev &W, const T *__restri
     }
     const float b1a = __ldg(W.b1 + 8 * j + 2 * t), b1b = __ldg(W.b1 + 8 * j + 2 * t + 1);
     const float b2a = __ldg(W.b2 + 8 * j + 2 * t), b2b = __ldg(W.b2 + 8 * j + 2 * t + 1);
-    __syncthreads();  // the raw strips are in the tile
-    if (threadIdx.x < 16) {
-        float s = 1.f;
-        if (row0 + (int)threadIdx.x < R) strip_finish(tile[threadIdx.x], s);  // rows past the border stay 0
-        sc[threadIdx.x] = s;
+    {
+        // row lr's 16 slots sit in 16 consecutive lanes; each of them sums the squares of the
+        // row's values in slot order (strip_finish's arithmetic) and scales its own value
+        const int lr = threadIdx.x >> 4, k = threadIdx.x & 15, r = row0 + lr;
+        float h = 0.f;
+        if (k < 15 && r < R) h = strip_value<T>(g, pitch, NX, edge_row(r, 0, 0, NX, NY), Store<T>::scaled, k);
+        float ss = 0.f;
+#pragma unroll
+        for (int q = 0; q < 15; ++q) {
+            const float x = __shfl_sync(0xffffffffu, h, (lane & 16) + q);
+            ss += x * x;
+        }
+        const float s = fmaxf(sqrtf(ss / 15.f), 1e-30f);
+        const float inv = 1.f / s;
+        tile[lr][k] = h * inv;  // 0 in slot 15 and in rows past the border
+        if (k == 0) sc[lr] = r < R ? s : 1.f;
     }
     __syncthreads();  // the scaled strips are in the tile
     // layer 1: tile j
