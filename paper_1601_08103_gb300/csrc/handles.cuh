@@ -43,10 +43,10 @@ struct lee_lbm {
     // the stream they are captured on
     std::map<std::pair<int, long long>, cudaGraphExec_t> exec;
     cudaStream_t cap = nullptr;
-    // learned edge: the arrival counters of the four corner cells in the one-launch step
+    // learned edge: the slots of the four corner cells in the one-launch step
     // (k_learned_step); with LEE_LEARNED_STREAMS=1 at create time the step runs as the network
     // and the border cells on `side` while the interior runs on the handle's stream instead
-    unsigned *corner = nullptr;
+    unsigned long long *corner = nullptr;
     bool learned_streams = false;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

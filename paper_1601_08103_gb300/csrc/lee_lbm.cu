@@ -20,7 +20,7 @@
 namespace lee {
 cudaError_t launch_mlp_boundary(const void *packed, int storage, const void *g, long long pitch, int NX, int NY, void *ghost,
                                 int L, cudaStream_t st);
-cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned *corner);
+cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned long long *corner);
 cudaError_t mlp_pack(const float *params_dev, void *packed, cudaStream_t st);
 extern const SetOps kOpsD1Q3, kOpsD2Q5, kOpsD2Q5Di, kOpsD3Q7, kOpsD3Q7Di, kOpsD3Q9, kOpsD3Q13, kOpsD3Q19;
 
@@ -485,8 +485,8 @@ lee_status lee_lbm_create(const lee_lbm_config *cfg, lee_lbm **out) {
     if (e == cudaSuccess && cfg->bc == LEE_BC_OPEN_LEARNED) {
         h->ghost_L = (int)(cfg->nx > cfg->ny ? cfg->nx : cfg->ny);
         e = cudaMalloc(&h->ghost, (cfg->storage == LEE_STORE_F64 ? 8 : 4) * 4 * (size_t)h->ghost_L);
-        if (e == cudaSuccess) e = cudaMalloc(&h->corner, 4 * sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->corner, 0, 4 * sizeof(unsigned), h->st);
+        if (e == cudaSuccess) e = cudaMalloc(&h->corner, 4 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->corner, 0, 4 * sizeof(unsigned long long), h->st);
     }
     if (e == cudaSuccess && o->step2_prepare && cfg->bc == LEE_BC_PERIODIC && cfg->storage == LEE_STORE_F32)
         e = o->step2_prepare();

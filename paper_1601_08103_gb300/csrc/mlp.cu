@@ -669,10 +669,12 @@ constexpr int learned_min_blocks() {
 //    pulls while the strips load, take the entering populations from lanes t == 0 by shuffle,
 //    store them into ghost[] and collide (k_edge_fixup's arithmetic);
 //  - a corner cell takes the entering populations of two rows, an x-edge one and a y-edge one,
-//    possibly in two blocks.  Each of the two lanes stores its value, fences and counts one
-//    arrival on the corner's counter; the lane whose arrival is the second of the step (an odd
-//    count before it: two arrivals per step, the counters start at 0) reads the other value from
-//    L2 and writes the corner.  Nothing waits;
+//    possibly in two blocks.  Each of the two lanes swaps its value (FP32, with a flag bit) into
+//    the corner's 64-bit slot; the lane that gets the other's value back (the second of the two)
+//    empties the slot and writes the corner.  FP64 values do not fit beside the flag: there each
+//    lane stores its value, fences and counts one arrival in the slot, and the second arrival of
+//    the step (an odd count before it: two arrivals per step from zero) reads the other value
+//    from L2.  Nothing waits;
 //  - the other blocks run the one-step stream-collide chunks over the interior cells, leaving the
 //    border unwritten (OpenEdge::skip_border).
 // The network blocks come first in the grid, so they are dispatched first and their dependent
@@ -681,7 +683,7 @@ template <class S, class T, int V>
 __global__ void __launch_bounds__(32 * kBoundaryWarps, learned_min_blocks<T, V>())
     k_learned_step(MlpDev W, const T *__restrict__ src, T *__restrict__ dst, GridDesc gd,
                    CollideCoef<typename Store<T>::C> cf, OpenEdge<typename Store<T>::C> ob,
-                   typename Store<T>::C *__restrict__ ghost, int L, unsigned *__restrict__ corner, int nnet) {
+                   typename Store<T>::C *__restrict__ ghost, int L, unsigned long long *__restrict__ corner, int nnet) {
     using C = typename Store<T>::C;
     static_assert(32 * kBoundaryWarps == 256, "the interior chunks take 256 threads per block");
     if ((int)blockIdx.x >= nnet) {
@@ -713,17 +715,29 @@ __global__ void __launch_bounds__(32 * kBoundaryWarps, learned_min_blocks<T, V>(
         edge_fixup_cell_from<S, T>(dst, gd, cf, [&](int, int) -> C { return gv; }, pulled, F.cx, F.cy);
         return;
     }
-    __threadfence();
-    const unsigned before = atomicAdd(corner + (F.cx == 0 ? 0 : 1) + (F.cy == 0 ? 0 : 2), 1u);
-    if ((before & 1u) == 0u) return;  // the corner's other row completes it
-    __threadfence();
-    edge_fixup_cell_from<S, T>(
-        dst, gd, cf, [&](int e, int k) -> C { return e == F.e ? gv : load_l2(ghost + e * L + k); }, pulled, F.cx,
-        F.cy);
+    unsigned long long *slot = corner + (F.cx == 0 ? 0 : 1) + (F.cy == 0 ? 0 : 2);
+    if constexpr (sizeof(C) == 4) {
+        // the value travels in the exchange: flag bit 32 marks a deposited value
+        const unsigned long long prev = atomicExch(slot, (1ULL << 32) | __float_as_uint(gv));
+        if ((prev >> 32) == 0ULL) return;  // first of the two: the other row completes the corner
+        *slot = 0ULL;                     // empty for the next step (only this lane touches it now)
+        const C other = __uint_as_float((unsigned)prev);
+        edge_fixup_cell_from<S, T>(dst, gd, cf, [&](int e, int) -> C { return e == F.e ? gv : other; }, pulled,
+                                   F.cx, F.cy);
+    } else {
+        // FP64 values do not fit beside a flag: count arrivals, then read the other value from L2
+        __threadfence();
+        const unsigned long long before = atomicAdd(slot, 1ULL);
+        if ((before & 1ULL) == 0ULL) return;  // the corner's other row completes it
+        __threadfence();
+        edge_fixup_cell_from<S, T>(
+            dst, gd, cf, [&](int e, int k) -> C { return e == F.e ? gv : load_l2(ghost + e * L + k); }, pulled,
+            F.cx, F.cy);
+    }
 }
 
 template <class S, class T, int V>
-cudaError_t launch_learned_v(const MlpDev &W, const StepLaunch &L, unsigned *corner) {
+cudaError_t launch_learned_v(const MlpDev &W, const StepLaunch &L, unsigned long long *corner) {
     using C = typename Store<T>::C;
     GridDesc gd;
     gd.nx = L.nx;
@@ -748,7 +762,7 @@ cudaError_t launch_learned_v(const MlpDev &W, const StepLaunch &L, unsigned *cor
 }
 
 template <class S>
-cudaError_t launch_learned_s(const MlpDev &W, const StepLaunch &L, unsigned *corner) {
+cudaError_t launch_learned_s(const MlpDev &W, const StepLaunch &L, unsigned long long *corner) {
     return with_store(L.storage, [&](auto *tp) -> cudaError_t {
         using T = std::remove_pointer_t<decltype(tp)>;
         constexpr int V = vec_width<S, T>();
@@ -759,8 +773,9 @@ cudaError_t launch_learned_s(const MlpDev &W, const StepLaunch &L, unsigned *cor
 
 // Called by lee_lbm_step for LEE_BC_OPEN_LEARNED (D2Q5): the whole step
 // in one launch of k_learned_step, reading L.src and writing L.dst and the entering populations
-// L.ghost[4][L.ghost_L]; corner = 4 arrival counters (zero at create, even between launches).
-cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned *corner) {
+// L.ghost[4][L.ghost_L]; corner = the 4 corner slots (zero at create and between launches, or
+// even arrival counts for FP64 storage).
+cudaError_t launch_learned_step(const void *packed, int set, const StepLaunch &L, unsigned long long *corner) {
     if (!L.ghost || !corner || L.nx < 3 || L.ny < 3 || L.nz != 1) return cudaErrorInvalidValue;
     const MlpDev W = mlp_dev(packed);
     if (set != LEE_D2Q5) return cudaErrorInvalidValue;  // the network is trained on this set only
