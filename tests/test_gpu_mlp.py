@@ -222,6 +222,42 @@ def test_learned_boundary_step_matches_oracle(gpu_lib, storage):
     assert err < (1e-5 if storage == "f64" else 3e-5), err
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_learned_boundary_16bit_storage_against_oracle(gpu_lib, storage):
+    """The learned step on 16-bit storage (scaled values, FP32 network and collision) against the
+    oracle's FP64 loop, 24 steps.  Every step rounds each stored population once to 16 bits
+    (relative error at most 2^-11 for FP16, 2^-8 for BF16); the bound allows twice that times
+    sqrt(n).  For FP16 the bound is also well below what the edge changes: the same run with
+    zero-incoming edges differs from the learned one by more than three times the bound."""
+    lee = gpu_lib
+    nx, ny, tau, n = 48, 33, 0.6, 24
+    s = oracle.velset("D2Q5")
+    c = [n_ / 2.5 for n_ in (nx, ny, 1)]
+    rho = inputs.gaussian_pulse((nx, ny, 1), 1e-3, 6.0, c, periodic=False)
+    u, th = inputs.zero_rest(2, nx * ny)
+    p = omlp.init_params(12) * 0.5
+    with lee.Solver("D2Q5", (nx, ny, 1), tau, storage=storage, bc="open_learned") as sv:
+        sv.set_boundary_mlp(p.astype(np.float32))
+        sv.init_fields(rho, u, th)
+        sv.step(n)
+        r_gpu = np.empty(nx * ny)
+        sv.moments(r_gpu)
+    g = oracle.equilibrium("D2Q5", rho, u, th)
+    for _ in range(n):
+        post = oracle.post_state("D2Q5", (nx, ny, 1), tau, g, bc="open_zero")
+        ghost = omlp.ghost_values(p, post, (nx, ny, 1), s.c, s.f)
+        g = oracle.step("D2Q5", (nx, ny, 1), tau, g, 1, bc="open_ghost", ghost=ghost)
+    r_ora = oracle.moments("D2Q5", g)[0]
+    unit = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
+    bound = 2 * unit * np.sqrt(n)
+    err = np.linalg.norm(r_gpu - r_ora) / np.linalg.norm(r_ora)
+    assert 0 < err < bound, (err, bound)
+    if storage == "f16":
+        gz = oracle.step("D2Q5", (nx, ny, 1), tau, oracle.equilibrium("D2Q5", rho, u, th), n, bc="open_zero")
+        edge = np.linalg.norm(oracle.moments("D2Q5", gz)[0] - r_ora) / np.linalg.norm(r_ora)
+        assert edge > 3 * bound, (edge, bound)
+
+
 def _learned_run(lee, monkeypatch, env, name, shape, storage, params, fields, calls):
     for k in ("LEE_LEARNED_STREAMS", "LEE_FORCE_SCALAR"):
         monkeypatch.delenv(k, raising=False)
